@@ -1,0 +1,196 @@
+/*
+ * agf2.h -- C ABI of the GB300 AGF2 library (moment-truncated auxiliary
+ * second-order Green's function theory, Backhouse, Santana-Bonilla & Booth,
+ * arXiv 2106.03508).
+ *
+ * Conventions shared by every entry point
+ * ---------------------------------------
+ *  - Array arguments are row-major FP64 pointers to DEVICE memory of the
+ *    handle's device unless stated otherwise.  The caller allocates them,
+ *    owns them and keeps them alive until the call returns.  Calls are
+ *    synchronous with respect to the host: outputs are complete on return.
+ *  - The library owns only the workspace held by the handle (grown on
+ *    demand, freed by agf2_destroy).  Work is issued on the handle's stream
+ *    (agf2_set_stream; default: the legacy default stream).
+ *  - Every function returns an int status (AGF2_OK = 0).  On failure the
+ *    outputs are unspecified and agf2_last_error(handle) returns a message.
+ *    No C++ exception crosses the ABI.
+ *  - The DF tensor L is [naux][nmo][nmo], each L[Q] symmetric, defining the
+ *    electron repulsion integrals (pq|rs) = sum_Q L[Q][p][q] L[Q][r][s].
+ *  - A handle is not thread safe; use one handle per host thread.
+ */
+#ifndef AGF2_H
+#define AGF2_H
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+/* ---- status codes ---- */
+#define AGF2_OK                 0
+#define AGF2_ERR_INVALID_ARG    1   /* bad size, null pointer, bad option      */
+#define AGF2_ERR_CUDA           2   /* a CUDA / cuSOLVER / cuBLAS call failed  */
+#define AGF2_ERR_OOM            3   /* workspace allocation failed             */
+#define AGF2_ERR_NOT_PD         4   /* U^(0) not positive definite (compress)  */
+#define AGF2_ERR_NO_CONVERGENCE 5   /* an iteration cap was reached            */
+#define AGF2_ERR_TIMEOUT        6   /* a bounded device wait gave up           */
+#define AGF2_ERR_UNSUPPORTED    7   /* precision/size not supported here       */
+
+/* ---- precision of the moment build ---- */
+#define AGF2_FP64   0   /* FP64 throughout                                     */
+#define AGF2_BF16X3 1   /* three-limb BF16 split products on tcgen05 tensor
+                           cores, FP32 accumulation, FP64 reduction            */
+
+typedef struct agf2_context* agf2_handle;
+
+/* Create a handle bound to CUDA device `device`; *out receives it. */
+int agf2_create(agf2_handle* out, int device);
+/* Free the handle and its workspace (NULL is accepted). */
+int agf2_destroy(agf2_handle h);
+/* Issue all further work on `stream` (a cudaStream_t passed as void*). */
+int agf2_set_stream(agf2_handle h, void* stream);
+/* Message of the last failure on this handle ("" if none).  The string is
+   owned by the handle and valid until its next call. */
+const char* agf2_last_error(agf2_handle h);
+
+/*
+ * One-body Hamiltonian of the synthetic closed-shell systems: h such that
+ * the Fock matrix of Eq. (fock_matrix) at the aufbau density
+ * D0 = diag(2,..,2,0,..,0) (nocc doubly occupied orbitals) equals diag(eps):
+ *     h = diag(eps) - (J[D0] - K[D0]/2).
+ *   L     [naux][nmo][nmo]  in
+ *   eps   [nmo]             in   orbital energies, occupied first
+ *   hcore [nmo][nmo]        out
+ */
+int agf2_hcore_from_mo_energies(agf2_handle h, const double* L, int naux, int nmo,
+                                const double* eps, int nocc, double* hcore);
+
+/*
+ * Self-energy moments, Eqs. (mp2_zeroth_moment), (mp2_first_moment) and
+ * their greater (particle) analogue, over the current Green's-function
+ * poles (the QMOs replace the MOs after the first iteration):
+ *   U_<^(n)_pq = sum_{ija} (pi|ja)[2(qi|ja) - (qj|ia)] (e_i + e_j - e_a)^n
+ *   U_>^(n)_pq = sum_{abi} (pa|bi)[2(qa|bi) - (qb|ai)] (e_a + e_b - e_i)^n
+ * with (px|yz) = sum_Q (L^Q C)_px (C^T L^Q C)_yz.  This is the only
+ * O(N^5) step of an AGF2 iteration.
+ *   L      [naux][nmo][nmo]   in
+ *   e      [nqmo]             in   pole energies; e < mu is occupied
+ *   C      [nmo][nqmo]        in   physical-space couplings of the poles
+ *   nmom   moment orders 0..nmom are produced (nmom >= 1)
+ *   precision AGF2_FP64 or AGF2_BF16X3
+ *   U_hole [nmom+1][nmo][nmo] out  (symmetrised)
+ *   U_part [nmom+1][nmo][nmo] out  (symmetrised)
+ * Needs at least one occupied and one virtual pole (else INVALID_ARG).
+ */
+int agf2_build_moments(agf2_handle h, const double* L, int naux, int nmo,
+                       const double* e, const double* C, int nqmo, double mu,
+                       int nmom, int precision, double* U_hole, double* U_part);
+
+/*
+ * Moment-conserving compression of one sector, Eq. (block_lanczos_chol_3)
+ * and the M-block below it: T T^T = U^(0) (lower Cholesky),
+ * M = T^-1 U^(1) T^-T, M = W diag(E) W^T, v = T W.  The nmo auxiliaries
+ * (E, v) reproduce U^(0) = v v^T and U^(1) = v diag(E) v^T.
+ *   U     [2][nmo][nmo]  in   U^(0), U^(1) of one sector
+ *   E_aux [nmo]          out  ascending
+ *   v_aux [nmo][nmo]     out  column k couples auxiliary k
+ * Returns AGF2_ERR_NOT_PD if U^(0) is not positive definite.
+ */
+int agf2_compress(agf2_handle h, const double* U, int nmo, double* E_aux, double* v_aux);
+
+typedef struct {
+    double tol_D;      /* convergence: max |D_new - D| (default 1e-10)        */
+    int    max_cycle;  /* Fock cycles (default 100)                           */
+    double shift_tol;  /* |n(delta) - nelec| target of the shift (1e-11)      */
+    double damping;    /* linear mixing of F before DIIS starts (0.3)         */
+    int    diis_start; /* first cycle whose pair enters DIIS (10)             */
+    int    diis_space; /* DIIS history length (6)                             */
+} agf2_fock_opts;
+
+typedef struct {
+    int    cycles;     /* Fock cycles run                                     */
+    int    converged;  /* 1 if max|dD| < tol_D                                */
+    int    nocc_qmo;   /* occupied poles (aufbau count)                       */
+    int    shift_evals;/* eigendecompositions spent on the shift, summed      */
+    double nerr;       /* n - nelec of the last shift solve                   */
+    double mu;         /* chemical potential (HOQMO/LUQMO midpoint)           */
+} agf2_fock_info;
+
+/* Fill `o` with the defaults listed above. */
+void agf2_fock_opts_default(agf2_fock_opts* o);
+
+/*
+ * Fock loop (density relaxation with the chemical potential held so that the
+ * non-idempotent density has nelec electrons; text after Eq. dyson_eq_eig):
+ * each cycle shifts all auxiliary energies by a common delta with
+ * n(delta) = nelec at fixed aufbau count, diagonalises the extended
+ * Hamiltonian [[F, v],[v^T, diag(E)]] (Eq. post_compression_h), sets
+ * D = 2 C_occ C_occ^T, and rebuilds F[D] by Eq. (fock_matrix).
+ *   hcore [nmo][nmo]        in
+ *   E_se  [nse]             in/out  auxiliary energies (returned shifted)
+ *   v_se  [nmo][nse]        in      auxiliary couplings
+ *   D     [nmo][nmo]        in/out  density
+ *   F     [nmo][nmo]        out     F[D] of the returned D
+ *   e_qmo [nmo+nse]         out     poles, ascending
+ *   C_qmo [nmo][nmo+nse]    out     physical part of the eigenvectors
+ *   opts  host pointer or NULL (defaults); info host pointer or NULL
+ * Returns AGF2_ERR_NO_CONVERGENCE (outputs valid) if the cap is reached.
+ */
+int agf2_fock_loop(agf2_handle h, const double* hcore, const double* L, int naux,
+                   int nmo, int nelec, double* E_se, const double* v_se, int nse,
+                   double* D, double* F, double* e_qmo, double* C_qmo,
+                   const agf2_fock_opts* opts, agf2_fock_info* info);
+
+typedef struct {
+    int    max_iter;   /* outer AGF2 iterations (default 50)                  */
+    double conv_tol;   /* |dE_tot| convergence (default 1e-8 Ha)              */
+    int    nmom;       /* moment order (only 1 is supported: AGF2(1,0))       */
+    int    precision;  /* AGF2_FP64 or AGF2_BF16X3                            */
+    double mix;        /* moment mixing U <- U_prev + mix (U - U_prev) (1.0)  */
+    int    resume;     /* 1: continue from the state kept in the handle       */
+    agf2_fock_opts fock;
+} agf2_opts;
+
+typedef struct {
+    double E_hf, E_1b, E_2b, E_tot;   /* Ha                                   */
+    double ip, ea, mu;                /* ip = -e_HOQMO, ea = -e_LUQMO         */
+    int    iterations;                /* outer iterations done in this call  */
+    int    converged;
+    int    nocc_qmo;
+    int    fock_cycles;               /* of the last iteration                */
+    double t_moments, t_compress, t_fock, t_energy;  /* seconds, summed      */
+    double flops_moments;             /* algorithmic flops of the moment builds */
+} agf2_result;
+
+/* Fill `o` with the defaults listed above. */
+void agf2_opts_default(agf2_opts* o);
+
+/*
+ * Full AGF2 iteration from the Hartree-Fock reference in the MO basis (poles
+ * e = eps0, C = I, D0 = aufbau density of nelec/2 orbitals): moments ->
+ * moment mixing -> compression of each sector -> Fock loop -> energies,
+ * until |dE_tot| < conv_tol or max_iter.  E_1b = Tr[D(h+F)]/2; E_2b is the
+ * Galitskii-Migdal sum over occupied poles x and particle-sector auxiliaries
+ * k of (C_x . v_k)^2 / (e_x - E_k).  The final state (poles, self-energy,
+ * density, mixing history) stays in the handle; with opts->resume = 1 the
+ * next call continues from it (eps0 is then ignored).
+ *   hcore [nmo][nmo], L [naux][nmo][nmo], eps0 [nmo]: device pointers
+ *   opts, out: host pointers (opts NULL = defaults)
+ * Returns AGF2_ERR_NO_CONVERGENCE (with *out filled) if max_iter is reached
+ * before convergence and max_iter > 1.
+ */
+int agf2_run(agf2_handle h, const double* hcore, const double* L, int naux, int nmo,
+             int nelec, const double* eps0, const agf2_opts* opts, agf2_result* out);
+
+/*
+ * Copy the Green's function kept in the handle after agf2_run: nqmo poles
+ * e [nqmo] and couplings C [nmo][nqmo] (device pointers sized for 3*nmo),
+ * the density D [nmo][nmo].  *nqmo receives the pole count (host pointer).
+ * Any output pointer may be NULL.
+ */
+int agf2_get_state(agf2_handle h, double* e, double* C, double* D, int* nqmo);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* AGF2_H */

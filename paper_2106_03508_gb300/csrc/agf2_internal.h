@@ -1,0 +1,76 @@
+// Internal declarations shared by the library's translation units.
+#pragma once
+#include <cuda_runtime.h>
+#include <cstdint>
+#include <string>
+
+namespace agf2 {
+
+// Generic strided, two-level-batched FP64 GEMM:
+//   C[z][m][n] = alpha * sum_k A[z][m][k] * B[z][k][n] + beta * C[z][m][n]
+// with element (m,k) of A at A + off_A(z) + m*sAm + k*sAk (likewise B, C) and
+// z = b1 * nb2 + b2, off_X(z) = b1*sX1 + b2*sX2.
+struct DGemm {
+  int M = 0, N = 0, K = 0;
+  const double* A = nullptr; long long sAm = 0, sAk = 0, sA1 = 0, sA2 = 0;
+  const double* B = nullptr; long long sBk = 0, sBn = 0, sB1 = 0, sB2 = 0;
+  double* C = nullptr;       long long sCm = 0, sCn = 0, sC1 = 0, sC2 = 0;
+  int nb1 = 1, nb2 = 1;
+  double alpha = 1.0, beta = 0.0;
+};
+cudaError_t dgemm(const DGemm& g, cudaStream_t s);
+
+// Moment epilogue of one block pair (I, J) of outer indices (FP64 path):
+// from X_IJ[p][(ii*nJ+jj)*n_in + c] = (p x_ii | y_jj c) and
+// X_JI[p][(jj*nI+ii)*n_in + c] (X_JI == X_IJ when diag) build
+//   Y [p][k]  = sqrt(cS) S  (k < K1),  sqrt(cD) D  (K1 <= k < 2 K1)
+//   Yw[p][k]  = Y[p][k] * (e_out[x] + e_out[y] - e_in[c])
+// with S = X_IJ + X_JI, D = X_IJ - X_JI, (cS, cD) = (1/4, 3/4) on the
+// diagonal block and (1/2, 3/2) off it; K1 = nI*nJ*n_in.
+cudaError_t sd_epilogue_fp64(const double* XIJ, const double* XJI, int nmo, int nI, int nJ,
+                             int n_in, const double* e_outI, const double* e_outJ,
+                             const double* e_in, bool diag, double* Y, double* Yw,
+                             cudaStream_t s);
+
+// Small FP64 kernels.
+cudaError_t gather_columns(const double* C, int nrow, int ncol_src, const int* idx, int n,
+                           double* out, cudaStream_t s);                // out[r][t] = C[r][idx[t]]
+cudaError_t gather_vec(const double* e, const int* idx, int n, double* out, cudaStream_t s);
+cudaError_t symmetrize(double* U, int n, int nmat, cudaStream_t s);   // U <- (U+U^T)/2
+cudaError_t axpby(double* y, const double* x, double a, double b, long long n, cudaStream_t s); // y = a*x + b*y
+cudaError_t build_extended_h(const double* F, const double* E, const double* v, double delta,
+                             int nmo, int nse, double* H, cudaStream_t s);
+// weights[x] = sum_{p<nmo} V[x*ld + p]^2   (V column-major eigenvectors, ld = n)
+cudaError_t column_weights(const double* V, int ld, int nmo, int ncol, double* w, cudaStream_t s);
+// out[p][x] = V[x*ld + p] for p<nmo, x<ncol (physical block, row-major)
+cudaError_t physical_block(const double* V, int ld, int nmo, int ncol, double* out, cudaStream_t s);
+// sum of a[i]*b[i] into *out (device scalar), deterministic two-pass.
+cudaError_t dot(const double* a, const double* b, long long n, double* out, double* scratch,
+                cudaStream_t s);
+// J_pq = sum_Q gamma_Q L[Q][p][q]
+cudaError_t coulomb_from_gamma(const double* L, const double* gamma, int naux, int nmo, double* J,
+                               cudaStream_t s);
+// gamma_Q = 2 sum_{r,k} Cocc[r][k] Y[r][Q][k]
+cudaError_t gamma_from_y(const double* Y, const double* Cocc, int nmo, int naux, int k,
+                         double* gamma, cudaStream_t s);
+// F = h + J - K/2  (elementwise)
+cudaError_t fock_combine(const double* h, const double* J, const double* K, long long n, double* F,
+                         cudaStream_t s);
+// GM: out = sum_{x<k, m<nse} V[x][m]^2 / (e[x] - E[m]), V = Cocc^T v (k x nse)
+cudaError_t gm_energy(const double* V, const double* e, const double* E, int k, int nse,
+                      double* out, double* scratch, cudaStream_t s);
+cudaError_t set_identity(double* A, int n, double scale, cudaStream_t s);
+cudaError_t diag_from_vec(const double* d, int n, double* A, cudaStream_t s);
+// max |a - b| into *out (device)
+cudaError_t max_abs_diff(const double* a, const double* b, long long n, double* out, double* scratch,
+                         cudaStream_t s);
+cudaError_t add_scalar(double* x, double a, int n, cudaStream_t s);
+
+// Split-precision (BF16x3 / tcgen05) moment build: see mixed.cu.
+struct MixedWorkspace;
+int mixed_build_moments(const double* L, int naux, int nmo, const double* Co, int o,
+                        const double* Cv, int v, const double* eo, const double* ev, int nmom,
+                        double* U_hole, double* U_part, void* ws_owner, std::string& err,
+                        cudaStream_t s);
+
+}  // namespace agf2

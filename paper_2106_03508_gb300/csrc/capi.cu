@@ -1,0 +1,961 @@
+// C ABI of the AGF2 library and the host-side sequencing of one AGF2
+// iteration (moments -> compression -> Fock loop -> energies).  All array
+// arithmetic runs in this library's CUDA kernels (fp64.cu, mixed.cu) or in
+// cuSOLVER/cuBLAS for the O(N^3) FP64 dense linear algebra of the
+// compression and the extended-Hamiltonian eigendecomposition; the host only
+// takes scalar decisions (aufbau count, bisection bracket, DIIS
+// coefficients, convergence).
+#include <cublas_v2.h>
+#include <cusolverDn.h>
+
+#include <algorithm>
+#include <chrono>
+#include <cmath>
+#include <cstdio>
+#include <cstring>
+#include <map>
+#include <string>
+#include <vector>
+
+#include "../../include/agf2.h"
+#include "agf2_internal.h"
+
+using namespace agf2;
+
+struct agf2_context {
+  int device = 0;
+  cudaStream_t stream = nullptr;
+  cusolverDnHandle_t solver = nullptr;
+  cublasHandle_t blas = nullptr;
+  std::string err;
+  struct Buf { void* p = nullptr; size_t bytes = 0; };
+  std::map<std::string, Buf> bufs;
+  int* dev_info = nullptr;
+  // ---- state kept between agf2_run calls ----
+  bool have_state = false;
+  int nmo = 0, nq = 0;
+  double mu = 0.0, E_prev = 0.0, E_hf = 0.0;
+  bool have_uprev = false;
+  int iter = 0;
+};
+
+namespace {
+
+struct Fail {
+  int code;
+};
+
+#define CK(call)                                                                           \
+  do {                                                                                     \
+    cudaError_t e_ = (call);                                                               \
+    if (e_ != cudaSuccess) {                                                               \
+      ctx->err = std::string(#call) + ": " + cudaGetErrorString(e_);                        \
+      throw Fail{AGF2_ERR_CUDA};                                                           \
+    }                                                                                      \
+  } while (0)
+#define CKS(call)                                                                          \
+  do {                                                                                     \
+    cusolverStatus_t e_ = (call);                                                          \
+    if (e_ != CUSOLVER_STATUS_SUCCESS) {                                                   \
+      ctx->err = std::string(#call) + ": cusolver status " + std::to_string((int)e_);      \
+      throw Fail{AGF2_ERR_CUDA};                                                           \
+    }                                                                                      \
+  } while (0)
+#define CKB(call)                                                                          \
+  do {                                                                                     \
+    cublasStatus_t e_ = (call);                                                            \
+    if (e_ != CUBLAS_STATUS_SUCCESS) {                                                     \
+      ctx->err = std::string(#call) + ": cublas status " + std::to_string((int)e_);        \
+      throw Fail{AGF2_ERR_CUDA};                                                           \
+    }                                                                                      \
+  } while (0)
+
+void fail(agf2_context* ctx, int code, const std::string& msg) {
+  ctx->err = msg;
+  throw Fail{code};
+}
+
+template <class T = double>
+T* ws(agf2_context* ctx, const char* name, size_t count) {
+  size_t bytes = std::max<size_t>(count * sizeof(T), 256);
+  auto& b = ctx->bufs[name];
+  if (b.bytes < bytes) {
+    if (b.p) {
+      cudaStreamSynchronize(ctx->stream);
+      cudaFree(b.p);
+      b.p = nullptr;
+      b.bytes = 0;
+    }
+    cudaError_t e = cudaMalloc(&b.p, bytes);
+    if (e != cudaSuccess) {
+      cudaGetLastError();
+      ctx->err = std::string("workspace '") + name + "' of " + std::to_string(bytes) +
+                 " bytes: " + cudaGetErrorString(e);
+      throw Fail{AGF2_ERR_OOM};
+    }
+    b.bytes = bytes;
+  }
+  return static_cast<T*>(b.p);
+}
+
+void sync(agf2_context* ctx) { CK(cudaStreamSynchronize(ctx->stream)); }
+
+template <class T>
+std::vector<T> to_host(agf2_context* ctx, const T* d, size_t n) {
+  std::vector<T> h(n);
+  if (n) {
+    CK(cudaMemcpyAsync(h.data(), d, n * sizeof(T), cudaMemcpyDeviceToHost, ctx->stream));
+    sync(ctx);
+  }
+  return h;
+}
+
+double scalar(agf2_context* ctx, const double* d) { return to_host(ctx, d, 1)[0]; }
+
+void check_dev_ptr(agf2_context* ctx, const void* p, const char* name) {
+  if (!p) fail(ctx, AGF2_ERR_INVALID_ARG, std::string(name) + " is NULL");
+  cudaPointerAttributes a;
+  cudaError_t e = cudaPointerGetAttributes(&a, p);
+  if (e != cudaSuccess) {
+    cudaGetLastError();
+    fail(ctx, AGF2_ERR_INVALID_ARG, std::string(name) + ": not a CUDA pointer");
+  }
+  if (a.type != cudaMemoryTypeDevice && a.type != cudaMemoryTypeManaged)
+    fail(ctx, AGF2_ERR_INVALID_ARG, std::string(name) + " must be device memory");
+}
+
+double seconds_since(std::chrono::steady_clock::time_point t0) {
+  return std::chrono::duration<double>(std::chrono::steady_clock::now() - t0).count();
+}
+
+// ---------------------------------------------------------------------------
+// Fock matrix, Eq. (fock_matrix), density fitted
+// ---------------------------------------------------------------------------
+// General D: J = sum_Q L^Q Tr(L^Q D),  K = sum_Q L^Q D L^Q.
+void fock_general(agf2_context* ctx, const double* h, const double* L, int naux, int n,
+                  const double* D, double* F) {
+  cudaStream_t s = ctx->stream;
+  const long long nn = (long long)n * n;
+  double* Z = ws(ctx, "fock_Z", (size_t)naux * nn);
+  double* J = ws(ctx, "fock_J", nn);
+  double* K = ws(ctx, "fock_K", nn);
+  double* gam = ws(ctx, "fock_gamma", naux);
+  // gamma_Q = sum_rs L[Q][r][s] D[r][s]: one-row GEMM (M = 1) over t = (r,s)
+  {
+    DGemm g;
+    g.M = naux; g.N = 1; g.K = (int)nn;
+    g.A = L; g.sAm = nn; g.sAk = 1;
+    g.B = D; g.sBk = 1; g.sBn = 0;
+    g.C = gam; g.sCm = 1; g.sCn = 0;
+    CK(dgemm(g, s));
+  }
+  CK(coulomb_from_gamma(L, gam, naux, n, J, s));
+  // Z[p][Q][r] = sum_s L[Q][p][s] D[s][r]
+  {
+    DGemm g;
+    g.M = n; g.N = n; g.K = n;
+    g.A = L; g.sAm = n; g.sAk = 1; g.sA1 = nn;
+    g.B = D; g.sBk = n; g.sBn = 1;
+    g.C = Z; g.sCm = (long long)naux * n; g.sCn = 1; g.sC1 = n;
+    g.nb1 = naux;
+    CK(dgemm(g, s));
+  }
+  // K[p][q] = sum_{(Q,r)} Z[p][(Q,r)] L[(Q,r)][q]
+  {
+    DGemm g;
+    g.M = n; g.N = n; g.K = naux * n;
+    g.A = Z; g.sAm = (long long)naux * n; g.sAk = 1;
+    g.B = L; g.sBk = n; g.sBn = 1;
+    g.C = K; g.sCm = n; g.sCn = 1;
+    CK(dgemm(g, s));
+  }
+  CK(fock_combine(h, J, K, nn, F, s));
+}
+
+// D = 2 Cocc Cocc^T with Cocc [n][k]:  J via gamma_Q = 2 sum Cocc . (L^Q Cocc),
+// K = 2 sum_Q (L^Q Cocc)(L^Q Cocc)^T.  Cost 4 N^2 k naux instead of 4 N^3 naux.
+void fock_cocc(agf2_context* ctx, const double* h, const double* L, int naux, int n,
+               const double* Cocc, int k, double* F) {
+  cudaStream_t s = ctx->stream;
+  const long long nn = (long long)n * n;
+  double* Y = ws(ctx, "fock_Y", (size_t)n * naux * k);
+  double* J = ws(ctx, "fock_J", nn);
+  double* K = ws(ctx, "fock_K", nn);
+  double* gam = ws(ctx, "fock_gamma", naux);
+  {
+    DGemm g;  // Y[p][Q][c] = sum_r L[Q][p][r] Cocc[r][c]
+    g.M = n; g.N = k; g.K = n;
+    g.A = L; g.sAm = n; g.sAk = 1; g.sA1 = nn;
+    g.B = Cocc; g.sBk = k; g.sBn = 1;
+    g.C = Y; g.sCm = (long long)naux * k; g.sCn = 1; g.sC1 = k;
+    g.nb1 = naux;
+    CK(dgemm(g, s));
+  }
+  CK(gamma_from_y(Y, Cocc, n, naux, k, gam, s));
+  CK(coulomb_from_gamma(L, gam, naux, n, J, s));
+  {
+    DGemm g;  // K = 2 Y Y^T over (Q, c)
+    g.M = n; g.N = n; g.K = naux * k;
+    g.A = Y; g.sAm = (long long)naux * k; g.sAk = 1;
+    g.B = Y; g.sBk = 1; g.sBn = (long long)naux * k;
+    g.C = K; g.sCm = n; g.sCn = 1;
+    g.alpha = 2.0;
+    CK(dgemm(g, s));
+  }
+  CK(fock_combine(h, J, K, nn, F, s));
+}
+
+// ---------------------------------------------------------------------------
+// Moments, Eqs. (mp2_zeroth_moment), (mp2_first_moment): FP64 path
+// ---------------------------------------------------------------------------
+struct Sector {
+  int n_out, n_in;
+  const double* Lx_out;  // [n_out][N][Q]
+  const double* Lpair;   // element (y, c, Q) at y*ys + c*cs + Q
+  long long ys, cs;
+  const double* e_out;
+  const double* e_in;
+};
+
+void sector_fp64(agf2_context* ctx, const Sector& S, int N, int naux, double* U0, double* U1) {
+  cudaStream_t s = ctx->stream;
+  const double budget_doubles = 2.0e8;  // 1.6 GB over the 6 block arrays
+  int nb = (int)std::floor(std::sqrt(budget_doubles / 6.0 / ((double)N * S.n_in)));
+  nb = std::max(1, std::min(nb, S.n_out));
+  const size_t K1max = (size_t)nb * nb * S.n_in;
+  double* XIJ = ws(ctx, "mom_XIJ", (size_t)N * K1max);
+  double* XJI = ws(ctx, "mom_XJI", (size_t)N * K1max);
+  double* Y = ws(ctx, "mom_Y", (size_t)N * 2 * K1max);
+  double* Yw = ws(ctx, "mom_Yw", (size_t)N * 2 * K1max);
+  const long long NQ = (long long)N * naux;
+  for (int I0 = 0; I0 < S.n_out; I0 += nb) {
+    const int nI = std::min(nb, S.n_out - I0);
+    for (int J0 = I0; J0 < S.n_out; J0 += nb) {
+      const int nJ = std::min(nb, S.n_out - J0);
+      const bool diag = (I0 == J0);
+      const long long K1 = (long long)nI * nJ * S.n_in;
+      auto pair_gemm = [&](int A0, int nA, int B0, int nB, double* X) {
+        DGemm g;  // X[p][(a*nB+b)*n_in + c] = sum_Q Lx_out[A0+a][p][Q] Lpair[B0+b][c][Q]
+        g.M = N; g.N = S.n_in; g.K = naux;
+        g.A = S.Lx_out + (long long)A0 * NQ; g.sAm = naux; g.sAk = 1; g.sA1 = NQ; g.sA2 = 0;
+        g.B = S.Lpair + (long long)B0 * S.ys; g.sBk = 1; g.sBn = S.cs; g.sB1 = 0; g.sB2 = S.ys;
+        g.C = X; g.sCm = K1; g.sCn = 1; g.sC1 = (long long)nB * S.n_in; g.sC2 = S.n_in;
+        g.nb1 = nA; g.nb2 = nB;
+        CK(dgemm(g, s));
+      };
+      pair_gemm(I0, nI, J0, nJ, XIJ);
+      if (!diag) pair_gemm(J0, nJ, I0, nI, XJI);
+      CK(sd_epilogue_fp64(XIJ, XJI, N, nI, nJ, S.n_in, S.e_out + I0, S.e_out + J0, S.e_in, diag, Y,
+                          Yw, s));
+      for (int n = 0; n < 2; ++n) {
+        DGemm g;  // U^(n) += Z Y^T, Z = Y (n = 0) or Yw (n = 1), K = 2 K1
+        g.M = N; g.N = N; g.K = (int)(2 * K1);
+        g.A = n == 0 ? Y : Yw; g.sAm = 2 * K1; g.sAk = 1;
+        g.B = Y; g.sBk = 1; g.sBn = 2 * K1;
+        g.C = n == 0 ? U0 : U1; g.sCm = N; g.sCn = 1;
+        g.beta = 1.0;
+        CK(dgemm(g, s));
+      }
+    }
+  }
+}
+
+struct PoleSplit {
+  int o = 0, v = 0;
+  std::vector<int> occ, vir;
+};
+
+PoleSplit split_poles(agf2_context* ctx, const double* e, int nq, double mu) {
+  PoleSplit ps;
+  std::vector<double> eh = to_host(ctx, e, nq);
+  for (int x = 0; x < nq; ++x) {
+    if (!std::isfinite(eh[x])) fail(ctx, AGF2_ERR_INVALID_ARG, "non-finite pole energy");
+    if (eh[x] < mu) ps.occ.push_back(x); else ps.vir.push_back(x);
+  }
+  ps.o = (int)ps.occ.size();
+  ps.v = (int)ps.vir.size();
+  return ps;
+}
+
+void build_moments_impl(agf2_context* ctx, const double* L, int naux, int N, const double* e,
+                        const double* C, int nq, double mu, int nmom, int precision,
+                        double* Uh, double* Up) {
+  cudaStream_t s = ctx->stream;
+  PoleSplit ps = split_poles(ctx, e, nq, mu);
+  if (ps.o < 1 || ps.v < 1) fail(ctx, AGF2_ERR_INVALID_ARG, "need occupied and virtual poles");
+  const int o = ps.o, v = ps.v;
+  int* idx = ws<int>(ctx, "mom_idx", nq);
+  std::vector<int> all(ps.occ);
+  all.insert(all.end(), ps.vir.begin(), ps.vir.end());
+  CK(cudaMemcpyAsync(idx, all.data(), nq * sizeof(int), cudaMemcpyHostToDevice, s));
+  double* Co = ws(ctx, "mom_Co", (size_t)N * o);
+  double* Cv = ws(ctx, "mom_Cv", (size_t)N * v);
+  double* eo = ws(ctx, "mom_eo", o);
+  double* ev = ws(ctx, "mom_ev", v);
+  CK(gather_columns(C, N, nq, idx, o, Co, s));
+  CK(gather_columns(C, N, nq, idx + o, v, Cv, s));
+  CK(gather_vec(e, idx, o, eo, s));
+  CK(gather_vec(e, idx + o, v, ev, s));
+  const long long NN = (long long)N * N;
+  const size_t mom_stride = (size_t)NN;
+  CK(cudaMemsetAsync(Uh, 0, (nmom + 1) * NN * sizeof(double), s));
+  CK(cudaMemsetAsync(Up, 0, (nmom + 1) * NN * sizeof(double), s));
+  if (precision == AGF2_BF16X3) {
+    int rc = mixed_build_moments(L, naux, N, Co, o, Cv, v, eo, ev, nmom, Uh, Up, ctx, ctx->err, s);
+    if (rc != AGF2_OK) throw Fail{rc};
+  } else {
+    const long long NQ = (long long)N * naux;
+    double* Lxo = ws(ctx, "mom_Lxo", (size_t)o * NQ);
+    double* Lxv = ws(ctx, "mom_Lxv", (size_t)v * NQ);
+    double* Lov = ws(ctx, "mom_Lov", (size_t)o * v * naux);
+    auto rot = [&](const double* Cx, int nx, double* out) {
+      DGemm g;  // out[x][p][Q] = sum_r Cx[r][x] L[Q][r][p]
+      g.M = nx; g.N = N; g.K = N;
+      g.A = Cx; g.sAm = 1; g.sAk = nx;
+      g.B = L; g.sBk = N; g.sBn = 1; g.sB1 = NN;
+      g.C = out; g.sCm = NQ; g.sCn = naux; g.sC1 = 1;
+      g.nb1 = naux;
+      CK(dgemm(g, s));
+    };
+    rot(Co, o, Lxo);
+    rot(Cv, v, Lxv);
+    {
+      DGemm g;  // Lov[j][a][Q] = sum_p Co[p][j] Lxv[a][p][Q]
+      g.M = o; g.N = v; g.K = N;
+      g.A = Co; g.sAm = 1; g.sAk = o;
+      g.B = Lxv; g.sBk = naux; g.sBn = NQ; g.sB1 = 1;
+      g.C = Lov; g.sCm = (long long)v * naux; g.sCn = naux; g.sC1 = 1;
+      g.nb1 = naux;
+      CK(dgemm(g, s));
+    }
+    Sector hole{o, v, Lxo, Lov, (long long)v * naux, (long long)naux, eo, ev};
+    Sector part{v, o, Lxv, Lov, (long long)naux, (long long)v * naux, ev, eo};
+    if (nmom != 1) fail(ctx, AGF2_ERR_UNSUPPORTED, "only nmom = 1 is implemented");
+    sector_fp64(ctx, hole, N, naux, Uh, Uh + mom_stride);
+    sector_fp64(ctx, part, N, naux, Up, Up + mom_stride);
+  }
+  CK(symmetrize(Uh, N, nmom + 1, s));
+  CK(symmetrize(Up, N, nmom + 1, s));
+  sync(ctx);
+}
+
+// ---------------------------------------------------------------------------
+// Compression, Eq. (block_lanczos_chol_3): T T^T = U0, M = T^-1 U1 T^-T
+// ---------------------------------------------------------------------------
+void syevd(agf2_context* ctx, double* A, int n, double* w) {
+  int lwork = 0;
+  CKS(cusolverDnDsyevd_bufferSize(ctx->solver, CUSOLVER_EIG_MODE_VECTOR, CUBLAS_FILL_MODE_LOWER, n,
+                                  A, n, w, &lwork));
+  double* work = ws(ctx, "syevd_work", (size_t)lwork);
+  CKS(cusolverDnDsyevd(ctx->solver, CUSOLVER_EIG_MODE_VECTOR, CUBLAS_FILL_MODE_LOWER, n, A, n, w,
+                       work, lwork, ctx->dev_info));
+  int info = 0;
+  CK(cudaMemcpyAsync(&info, ctx->dev_info, sizeof(int), cudaMemcpyDeviceToHost, ctx->stream));
+  sync(ctx);
+  if (info != 0) fail(ctx, AGF2_ERR_CUDA, "syevd failed to converge, info " + std::to_string(info));
+}
+
+void compress_impl(agf2_context* ctx, const double* U, int n, double* E, double* v_rowmajor,
+                   long long ldv) {
+  cudaStream_t s = ctx->stream;
+  const long long nn = (long long)n * n;
+  double* T = ws(ctx, "cmp_T", nn);
+  double* M = ws(ctx, "cmp_M", nn);
+  double* W = ws(ctx, "cmp_W", nn);
+  CK(cudaMemcpyAsync(T, U, nn * sizeof(double), cudaMemcpyDeviceToDevice, s));
+  CK(cudaMemcpyAsync(M, U + nn, nn * sizeof(double), cudaMemcpyDeviceToDevice, s));
+  // column-major view: U0, U1 symmetric, so the arrays are their own transposes
+  int lwork = 0;
+  CKS(cusolverDnDpotrf_bufferSize(ctx->solver, CUBLAS_FILL_MODE_LOWER, n, T, n, &lwork));
+  double* work = ws(ctx, "potrf_work", (size_t)lwork);
+  CKS(cusolverDnDpotrf(ctx->solver, CUBLAS_FILL_MODE_LOWER, n, T, n, work, lwork, ctx->dev_info));
+  int info = 0;
+  CK(cudaMemcpyAsync(&info, ctx->dev_info, sizeof(int), cudaMemcpyDeviceToHost, s));
+  sync(ctx);
+  if (info != 0)
+    fail(ctx, AGF2_ERR_NOT_PD,
+         "U^(0) is not positive definite (potrf info " + std::to_string(info) + ")");
+  const double one = 1.0;
+  // M <- T^-1 U1, then M <- M T^-T
+  CKB(cublasDtrsm(ctx->blas, CUBLAS_SIDE_LEFT, CUBLAS_FILL_MODE_LOWER, CUBLAS_OP_N,
+                  CUBLAS_DIAG_NON_UNIT, n, n, &one, T, n, M, n));
+  CKB(cublasDtrsm(ctx->blas, CUBLAS_SIDE_RIGHT, CUBLAS_FILL_MODE_LOWER, CUBLAS_OP_T,
+                  CUBLAS_DIAG_NON_UNIT, n, n, &one, T, n, M, n));
+  CK(symmetrize(M, n, 1, s));
+  syevd(ctx, M, n, E);
+  // v = T W (column-major), W = eigenvectors in M
+  CKB(cublasDtrmm(ctx->blas, CUBLAS_SIDE_LEFT, CUBLAS_FILL_MODE_LOWER, CUBLAS_OP_N,
+                  CUBLAS_DIAG_NON_UNIT, n, n, &one, T, n, M, n, W, n));
+  // row-major v[p][k] = W_cm[p + k n]  ->  physical_block does exactly this transpose
+  if (ldv == n) {
+    CK(physical_block(W, n, n, n, v_rowmajor, s));
+  } else {
+    double* tmp = ws(ctx, "cmp_vrm", nn);
+    CK(physical_block(W, n, n, n, tmp, s));
+    CK(cudaMemcpy2DAsync(v_rowmajor, ldv * sizeof(double), tmp, n * sizeof(double),
+                         n * sizeof(double), n, cudaMemcpyDeviceToDevice, s));
+  }
+  sync(ctx);
+}
+
+// ---------------------------------------------------------------------------
+// Extended Hamiltonian, chemical potential and the Fock loop
+// ---------------------------------------------------------------------------
+struct Eig {
+  double* V;  // column-major eigenvectors [n][n]
+  double* w;  // eigenvalues
+  int n;
+};
+
+Eig diag_extended(agf2_context* ctx, const double* F, const double* E, const double* v, double delta,
+                  int nmo, int nse) {
+  const int n = nmo + nse;
+  Eig r{ws(ctx, "ext_H", (size_t)n * n), ws(ctx, "ext_w", n), n};
+  CK(build_extended_h(F, E, v, delta, nmo, nse, r.V, ctx->stream));
+  syevd(ctx, r.V, n, r.w);
+  return r;
+}
+
+std::vector<double> pole_weights(agf2_context* ctx, const Eig& eg, int nmo) {
+  double* wt = ws(ctx, "ext_wt", eg.n);
+  CK(column_weights(eg.V, eg.n, nmo, eg.n, wt, ctx->stream));
+  return to_host(ctx, wt, eg.n);
+}
+
+struct Aufbau {
+  int k;
+  double mu, n;
+};
+
+Aufbau aufbau(const std::vector<double>& e, const std::vector<double>& wt, int nelec) {
+  const int n = (int)e.size();
+  double cum = 0.0, best = std::fabs(0.0 - nelec);
+  int k = 0;
+  std::vector<double> c(n + 1, 0.0);
+  for (int x = 0; x < n; ++x) {
+    cum += 2.0 * wt[x];
+    c[x + 1] = cum;
+  }
+  for (int x = 1; x <= n; ++x) {
+    const double d = std::fabs(c[x] - nelec);
+    if (d < best) { best = d; k = x; }
+  }
+  k = std::min(std::max(k, 1), n - 1);
+  return Aufbau{k, 0.5 * (e[k - 1] + e[k]), c[k]};
+}
+
+double nelec_fixed_k(const std::vector<double>& wt, int k) {
+  double s = 0.0;
+  for (int x = 0; x < k; ++x) s += wt[x];
+  return 2.0 * s;
+}
+
+struct Shift {
+  double delta, nerr;
+  int evals;
+  bool converged;
+};
+
+// Common shift of the auxiliary energies so that n(delta; k) = nelec with k
+// the aufbau count at delta = 0; bracket by doubling, then bisection.
+Shift solve_shift(agf2_context* ctx, const double* F, const double* E, const double* v, int nmo,
+                  int nse, int nelec, double tol) {
+  auto eval = [&](double d, int k) {
+    Eig eg = diag_extended(ctx, F, E, v, d, nmo, nse);
+    return nelec_fixed_k(pole_weights(ctx, eg, nmo), k) - nelec;
+  };
+  Eig e0 = diag_extended(ctx, F, E, v, 0.0, nmo, nse);
+  std::vector<double> wt = pole_weights(ctx, e0, nmo);
+  std::vector<double> ev = to_host(ctx, e0.w, e0.n);
+  const int k = aufbau(ev, wt, nelec).k;
+  int evals = 1;
+  const double f0 = nelec_fixed_k(wt, k) - nelec;
+  if (std::fabs(f0) < tol) return Shift{0.0, f0, evals, true};
+  bool has_lo = f0 < 0, has_hi = !has_lo;
+  double lo = 0, flo = f0, hi = 0, fhi = f0;
+  double step = 1.0;
+  for (int it = 0; it < 60; ++it) {
+    const double d = has_lo ? step : -step;
+    const double f = eval(d, k);
+    ++evals;
+    if (f < 0) { lo = d; flo = f; has_lo = true; } else { hi = d; fhi = f; has_hi = true; }
+    if (has_lo && has_hi) break;
+    step *= 2.0;
+  }
+  if (!(has_lo && has_hi)) return Shift{has_lo ? lo : hi, has_lo ? flo : fhi, evals, false};
+  double best = std::fabs(flo) < std::fabs(fhi) ? lo : hi;
+  double fbest = std::fabs(flo) < std::fabs(fhi) ? flo : fhi;
+  for (int it = 0; it < 200; ++it) {
+    if (std::fabs(fbest) < tol || hi - lo < 1e-14) break;
+    const double mid = 0.5 * (lo + hi);
+    const double f = eval(mid, k);
+    ++evals;
+    if (std::fabs(f) < std::fabs(fbest)) { best = mid; fbest = f; }
+    if (f < 0) lo = mid; else hi = mid;
+  }
+  return Shift{best, fbest, evals, std::fabs(fbest) < tol};
+}
+
+// Pulay extrapolation coefficients from B_ab = <r_a, r_b> (host solve of the
+// bordered (m+1)x(m+1) system by Gaussian elimination with partial pivoting).
+std::vector<double> diis_coeffs(const std::vector<double>& B, int m) {
+  const int n = m + 1;
+  std::vector<double> A((size_t)n * n, 0.0), b(n, 0.0);
+  for (int i = 0; i < m; ++i)
+    for (int j = 0; j < m; ++j) A[i * n + j] = B[i * m + j];
+  for (int i = 0; i < m; ++i) { A[m * n + i] = 1.0; A[i * n + m] = 1.0; }
+  b[m] = 1.0;
+  for (int c = 0; c < n; ++c) {
+    int p = c;
+    for (int r = c + 1; r < n; ++r)
+      if (std::fabs(A[r * n + c]) > std::fabs(A[p * n + c])) p = r;
+    if (p != c) {
+      for (int j = 0; j < n; ++j) std::swap(A[c * n + j], A[p * n + j]);
+      std::swap(b[c], b[p]);
+    }
+    const double piv = A[c * n + c];
+    if (piv == 0.0) continue;
+    for (int r = c + 1; r < n; ++r) {
+      const double f = A[r * n + c] / piv;
+      if (f == 0.0) continue;
+      for (int j = c; j < n; ++j) A[r * n + j] -= f * A[c * n + j];
+      b[r] -= f * b[c];
+    }
+  }
+  std::vector<double> x(n, 0.0);
+  for (int r = n - 1; r >= 0; --r) {
+    double sacc = b[r];
+    for (int j = r + 1; j < n; ++j) sacc -= A[r * n + j] * x[j];
+    x[r] = A[r * n + r] != 0.0 ? sacc / A[r * n + r] : 0.0;
+  }
+  x.resize(m);
+  return x;
+}
+
+struct FockOut {
+  int cycles, converged, k, evals;
+  double mu, nerr;
+};
+
+// Fock loop: see agf2_fock_loop in agf2.h.  F_in holds the initial F[D] on
+// entry; on exit D, F (= F[D]), e_qmo, C_qmo are written.
+FockOut fock_loop_impl(agf2_context* ctx, const double* h, const double* L, int naux, int nmo,
+                       int nelec, double* E, const double* v, int nse, double* D, double* F,
+                       double* e_qmo, double* C_qmo, const agf2_fock_opts& o) {
+  cudaStream_t s = ctx->stream;
+  const int n = nmo + nse;
+  const long long nn = (long long)nmo * nmo;
+  const int space = std::max(0, o.diis_space);
+  double* Fin = ws(ctx, "fl_Fin", nn);
+  double* Fout = ws(ctx, "fl_Fout", nn);
+  double* Dn = ws(ctx, "fl_Dnew", nn);
+  double* Cphys = ws(ctx, "fl_Cphys", (size_t)nmo * n);
+  double* hF = ws(ctx, "fl_histF", (size_t)std::max(space, 1) * nn);
+  double* hR = ws(ctx, "fl_histR", (size_t)std::max(space, 1) * nn);
+  double* red = ws(ctx, "fl_red", 1024);
+  double* dots = ws(ctx, "fl_dots", 64);
+  CK(cudaMemcpyAsync(Fin, F, nn * sizeof(double), cudaMemcpyDeviceToDevice, s));
+  int nh = 0, head = 0;  // ring buffer of history entries
+  std::vector<int> order;
+  FockOut out{0, 0, 0, 0, 0.0, 0.0};
+  for (int cyc = 1; cyc <= o.max_cycle; ++cyc) {
+    out.cycles = cyc;
+    Shift sh = solve_shift(ctx, Fin, E, v, nmo, nse, nelec, o.shift_tol);
+    out.evals += sh.evals;
+    out.nerr = sh.nerr;
+    CK(add_scalar(E, sh.delta, nse, s));
+    Eig eg = diag_extended(ctx, Fin, E, v, 0.0, nmo, nse);
+    std::vector<double> wt = pole_weights(ctx, eg, nmo);
+    std::vector<double> ev = to_host(ctx, eg.w, n);
+    Aufbau ab = aufbau(ev, wt, nelec);
+    out.k = ab.k;
+    out.mu = ab.mu;
+    CK(physical_block(eg.V, n, nmo, n, Cphys, s));  // Cphys[p][x]
+    CK(cudaMemcpyAsync(e_qmo, eg.w, n * sizeof(double), cudaMemcpyDeviceToDevice, s));
+    CK(cudaMemcpyAsync(C_qmo, Cphys, (size_t)nmo * n * sizeof(double), cudaMemcpyDeviceToDevice, s));
+    // occupied block Cocc[p][x<k] = Cphys with leading dimension n
+    double* Cocc = ws(ctx, "fl_Cocc", (size_t)nmo * ab.k);
+    CK(cudaMemcpy2DAsync(Cocc, ab.k * sizeof(double), Cphys, n * sizeof(double),
+                         ab.k * sizeof(double), nmo, cudaMemcpyDeviceToDevice, s));
+    {
+      DGemm g;  // D_new = 2 Cocc Cocc^T
+      g.M = nmo; g.N = nmo; g.K = ab.k;
+      g.A = Cocc; g.sAm = ab.k; g.sAk = 1;
+      g.B = Cocc; g.sBk = 1; g.sBn = ab.k;
+      g.C = Dn; g.sCm = nmo; g.sCn = 1;
+      g.alpha = 2.0;
+      CK(dgemm(g, s));
+    }
+    fock_cocc(ctx, h, L, naux, nmo, Cocc, ab.k, Fout);
+    CK(max_abs_diff(Dn, D, nn, red + 512, red, s));
+    const double dD = scalar(ctx, red + 512);
+    CK(cudaMemcpyAsync(D, Dn, nn * sizeof(double), cudaMemcpyDeviceToDevice, s));
+    if (dD < o.tol_D) {
+      out.converged = 1;
+      break;
+    }
+    if (cyc >= o.diis_start && space > 1) {
+      // new entry (F_in, F_out - F_in) into the ring
+      const int slot = (nh < space) ? nh : head;
+      CK(cudaMemcpyAsync(hF + slot * nn, Fin, nn * sizeof(double), cudaMemcpyDeviceToDevice, s));
+      CK(cudaMemcpyAsync(hR + slot * nn, Fout, nn * sizeof(double), cudaMemcpyDeviceToDevice, s));
+      CK(axpby(hR + slot * nn, Fin, -1.0, 1.0, nn, s));
+      if (nh < space) { order.push_back(slot); ++nh; }
+      else { order.erase(order.begin()); order.push_back(slot); head = (head + 1) % space; }
+    }
+    if (nh > 1) {
+      const int m = nh;
+      for (int a = 0; a < m; ++a)
+        for (int b = a; b < m; ++b)
+          CK(dot(hR + order[a] * nn, hR + order[b] * nn, nn, dots + a * m + b, red, s));
+      std::vector<double> Bh = to_host(ctx, dots, (size_t)m * m);
+      for (int a = 0; a < m; ++a)
+        for (int b = 0; b < a; ++b) Bh[a * m + b] = Bh[b * m + a];
+      std::vector<double> c = diis_coeffs(Bh, m);
+      CK(cudaMemsetAsync(Fin, 0, nn * sizeof(double), s));
+      for (int a = 0; a < m; ++a) {
+        CK(axpby(Fin, hF + order[a] * nn, c[a], 1.0, nn, s));
+        CK(axpby(Fin, hR + order[a] * nn, c[a], 1.0, nn, s));
+      }
+    } else {
+      // F_in <- F_in + damping (F_out - F_in)
+      CK(axpby(Fin, Fout, o.damping, 1.0 - o.damping, nn, s));
+    }
+  }
+  fock_cocc(ctx, h, L, naux, nmo, ws(ctx, "fl_Cocc", 1), out.k, F);
+  sync(ctx);
+  return out;
+}
+
+agf2_fock_opts fock_defaults() {
+  agf2_fock_opts o;
+  o.tol_D = 1e-10;
+  o.max_cycle = 100;
+  o.shift_tol = 1e-11;
+  o.damping = 0.3;
+  o.diis_start = 10;
+  o.diis_space = 6;
+  return o;
+}
+
+template <class Fn>
+int guarded(agf2_handle h, Fn&& fn) {
+  if (!h) return AGF2_ERR_INVALID_ARG;
+  agf2_context* ctx = h;
+  ctx->err.clear();
+  try {
+    cudaError_t e = cudaSetDevice(ctx->device);
+    if (e != cudaSuccess) fail(ctx, AGF2_ERR_CUDA, cudaGetErrorString(e));
+    fn(ctx);
+    return AGF2_OK;
+  } catch (const Fail& f) {
+    return f.code;
+  } catch (const std::exception& ex) {
+    ctx->err = ex.what();
+    return AGF2_ERR_CUDA;
+  } catch (...) {
+    ctx->err = "unknown exception";
+    return AGF2_ERR_CUDA;
+  }
+}
+
+}  // namespace
+
+// ===========================================================================
+// C ABI
+// ===========================================================================
+extern "C" {
+
+int agf2_create(agf2_handle* out, int device) {
+  if (!out) return AGF2_ERR_INVALID_ARG;
+  *out = nullptr;
+  int ndev = 0;
+  if (cudaGetDeviceCount(&ndev) != cudaSuccess || device < 0 || device >= ndev) {
+    cudaGetLastError();
+    return AGF2_ERR_INVALID_ARG;
+  }
+  auto* ctx = new agf2_context();
+  ctx->device = device;
+  if (cudaSetDevice(device) != cudaSuccess) { delete ctx; return AGF2_ERR_CUDA; }
+  if (cusolverDnCreate(&ctx->solver) != CUSOLVER_STATUS_SUCCESS) { delete ctx; return AGF2_ERR_CUDA; }
+  if (cublasCreate(&ctx->blas) != CUBLAS_STATUS_SUCCESS) {
+    cusolverDnDestroy(ctx->solver);
+    delete ctx;
+    return AGF2_ERR_CUDA;
+  }
+  if (cudaMalloc(&ctx->dev_info, sizeof(int)) != cudaSuccess) {
+    cublasDestroy(ctx->blas);
+    cusolverDnDestroy(ctx->solver);
+    delete ctx;
+    return AGF2_ERR_OOM;
+  }
+  cusolverDnSetStream(ctx->solver, ctx->stream);
+  cublasSetStream(ctx->blas, ctx->stream);
+  *out = ctx;
+  return AGF2_OK;
+}
+
+int agf2_destroy(agf2_handle h) {
+  if (!h) return AGF2_OK;
+  cudaSetDevice(h->device);
+  if (h->stream) cudaStreamSynchronize(h->stream);
+  for (auto& kv : h->bufs)
+    if (kv.second.p) cudaFree(kv.second.p);
+  if (h->dev_info) cudaFree(h->dev_info);
+  if (h->blas) cublasDestroy(h->blas);
+  if (h->solver) cusolverDnDestroy(h->solver);
+  delete h;
+  return AGF2_OK;
+}
+
+int agf2_set_stream(agf2_handle h, void* stream) {
+  return guarded(h, [&](agf2_context* ctx) {
+    ctx->stream = static_cast<cudaStream_t>(stream);
+    CKS(cusolverDnSetStream(ctx->solver, ctx->stream));
+    CKB(cublasSetStream(ctx->blas, ctx->stream));
+  });
+}
+
+const char* agf2_last_error(agf2_handle h) { return h ? h->err.c_str() : "null handle"; }
+
+void agf2_fock_opts_default(agf2_fock_opts* o) {
+  if (o) *o = fock_defaults();
+}
+
+void agf2_opts_default(agf2_opts* o) {
+  if (!o) return;
+  o->max_iter = 50;
+  o->conv_tol = 1e-8;
+  o->nmom = 1;
+  o->precision = AGF2_FP64;
+  o->mix = 1.0;
+  o->resume = 0;
+  o->fock = fock_defaults();
+}
+
+int agf2_hcore_from_mo_energies(agf2_handle h, const double* L, int naux, int nmo,
+                                const double* eps, int nocc, double* hcore) {
+  return guarded(h, [&](agf2_context* ctx) {
+    if (naux < 1 || nmo < 2 || nocc < 1 || nocc >= nmo)
+      fail(ctx, AGF2_ERR_INVALID_ARG, "need naux >= 1 and 0 < nocc < nmo");
+    check_dev_ptr(ctx, L, "L");
+    check_dev_ptr(ctx, eps, "eps");
+    check_dev_ptr(ctx, hcore, "hcore");
+    cudaStream_t s = ctx->stream;
+    const long long nn = (long long)nmo * nmo;
+    double* D0 = ws(ctx, "hc_D0", nn);
+    double* Z = ws(ctx, "hc_zero", nn);
+    double* F = ws(ctx, "hc_F", nn);
+    std::vector<double> d(nmo, 0.0);
+    for (int i = 0; i < nocc; ++i) d[i] = 2.0;
+    double* dv = ws(ctx, "hc_d", nmo);
+    CK(cudaMemcpyAsync(dv, d.data(), nmo * sizeof(double), cudaMemcpyHostToDevice, s));
+    CK(diag_from_vec(dv, nmo, D0, s));
+    CK(cudaMemsetAsync(Z, 0, nn * sizeof(double), s));
+    fock_general(ctx, Z, L, naux, nmo, D0, F);  // F = J - K/2
+    CK(diag_from_vec(eps, nmo, hcore, s));
+    CK(axpby(hcore, F, -1.0, 1.0, nn, s));
+    sync(ctx);
+  });
+}
+
+int agf2_build_moments(agf2_handle h, const double* L, int naux, int nmo, const double* e,
+                       const double* C, int nqmo, double mu, int nmom, int precision,
+                       double* U_hole, double* U_part) {
+  return guarded(h, [&](agf2_context* ctx) {
+    if (naux < 1 || nmo < 1 || nqmo < 2 || nmom < 1)
+      fail(ctx, AGF2_ERR_INVALID_ARG, "bad sizes");
+    if (nmom != 1) fail(ctx, AGF2_ERR_UNSUPPORTED, "only nmom = 1 (AGF2(1,0)) is implemented");
+    if (precision != AGF2_FP64 && precision != AGF2_BF16X3)
+      fail(ctx, AGF2_ERR_INVALID_ARG, "unknown precision");
+    check_dev_ptr(ctx, L, "L");
+    check_dev_ptr(ctx, e, "e");
+    check_dev_ptr(ctx, C, "C");
+    check_dev_ptr(ctx, U_hole, "U_hole");
+    check_dev_ptr(ctx, U_part, "U_part");
+    build_moments_impl(ctx, L, naux, nmo, e, C, nqmo, mu, nmom, precision, U_hole, U_part);
+  });
+}
+
+int agf2_compress(agf2_handle h, const double* U, int nmo, double* E_aux, double* v_aux) {
+  return guarded(h, [&](agf2_context* ctx) {
+    if (nmo < 1) fail(ctx, AGF2_ERR_INVALID_ARG, "nmo < 1");
+    check_dev_ptr(ctx, U, "U");
+    check_dev_ptr(ctx, E_aux, "E_aux");
+    check_dev_ptr(ctx, v_aux, "v_aux");
+    compress_impl(ctx, U, nmo, E_aux, v_aux, nmo);
+  });
+}
+
+int agf2_fock_loop(agf2_handle h, const double* hcore, const double* L, int naux, int nmo,
+                   int nelec, double* E_se, const double* v_se, int nse, double* D, double* F,
+                   double* e_qmo, double* C_qmo, const agf2_fock_opts* opts,
+                   agf2_fock_info* info) {
+  int rc_conv = AGF2_OK;
+  int rc = guarded(h, [&](agf2_context* ctx) {
+    if (naux < 1 || nmo < 1 || nse < 0 || nelec < 1 || nelec > 2 * (nmo + nse))
+      fail(ctx, AGF2_ERR_INVALID_ARG, "bad sizes");
+    for (auto p : {(const void*)hcore, (const void*)L, (const void*)E_se, (const void*)v_se,
+                   (const void*)D, (const void*)F, (const void*)e_qmo, (const void*)C_qmo})
+      check_dev_ptr(ctx, p, "argument");
+    agf2_fock_opts o = opts ? *opts : fock_defaults();
+    if (o.max_cycle < 1) fail(ctx, AGF2_ERR_INVALID_ARG, "max_cycle < 1");
+    fock_general(ctx, hcore, L, naux, nmo, D, F);
+    FockOut fo = fock_loop_impl(ctx, hcore, L, naux, nmo, nelec, E_se, v_se, nse, D, F, e_qmo,
+                                C_qmo, o);
+    if (info) {
+      info->cycles = fo.cycles;
+      info->converged = fo.converged;
+      info->nocc_qmo = fo.k;
+      info->shift_evals = fo.evals;
+      info->nerr = fo.nerr;
+      info->mu = fo.mu;
+    }
+    if (!fo.converged) rc_conv = AGF2_ERR_NO_CONVERGENCE;
+  });
+  return rc != AGF2_OK ? rc : rc_conv;
+}
+
+int agf2_run(agf2_handle h, const double* hcore, const double* L, int naux, int nmo, int nelec,
+             const double* eps0, const agf2_opts* opts, agf2_result* out) {
+  int rc_conv = AGF2_OK;
+  int rc = guarded(h, [&](agf2_context* ctx) {
+    if (!out) fail(ctx, AGF2_ERR_INVALID_ARG, "out is NULL");
+    agf2_opts o;
+    agf2_opts_default(&o);
+    if (opts) o = *opts;
+    if (naux < 1 || nmo < 2 || nelec < 2 || nelec % 2 || nelec >= 2 * nmo || o.max_iter < 1)
+      fail(ctx, AGF2_ERR_INVALID_ARG, "bad sizes or options");
+    if (o.nmom != 1) fail(ctx, AGF2_ERR_UNSUPPORTED, "only nmom = 1 (AGF2(1,0)) is implemented");
+    check_dev_ptr(ctx, hcore, "hcore");
+    check_dev_ptr(ctx, L, "L");
+    cudaStream_t s = ctx->stream;
+    const int N = nmo, nse = 2 * nmo, nq_max = 3 * nmo;
+    const long long NN = (long long)N * N;
+    double* e = ws(ctx, "st_e", nq_max);
+    double* C = ws(ctx, "st_C", (size_t)N * nq_max);
+    double* D = ws(ctx, "st_D", NN);
+    double* F = ws(ctx, "st_F", NN);
+    double* U = ws(ctx, "st_U", 4 * NN);
+    double* Uprev = ws(ctx, "st_Uprev", 4 * NN);
+    double* Ese = ws(ctx, "st_Ese", nse);
+    double* vse = ws(ctx, "st_vse", (size_t)N * nse);
+    double* eq = ws(ctx, "st_eq", nq_max);
+    double* Cq = ws(ctx, "st_Cq", (size_t)N * nq_max);
+    double* red = ws(ctx, "st_red", 1024);
+    double* V = ws(ctx, "st_V", (size_t)nq_max * N);
+    const int nocc = nelec / 2;
+    if (!o.resume || !ctx->have_state || ctx->nmo != N) {
+      check_dev_ptr(ctx, eps0, "eps0");
+      std::vector<double> e0 = to_host(ctx, eps0, N);
+      CK(cudaMemcpyAsync(e, eps0, N * sizeof(double), cudaMemcpyDeviceToDevice, s));
+      CK(set_identity(C, N, 1.0, s));
+      std::vector<double> d(N, 0.0);
+      for (int i = 0; i < nocc; ++i) d[i] = 2.0;
+      double* dv = ws(ctx, "st_d0", N);
+      CK(cudaMemcpyAsync(dv, d.data(), N * sizeof(double), cudaMemcpyHostToDevice, s));
+      CK(diag_from_vec(dv, N, D, s));
+      fock_general(ctx, hcore, L, naux, N, D, F);
+      CK(dot(D, hcore, NN, red + 512, red, s));
+      CK(dot(D, F, NN, red + 513, red, s));
+      std::vector<double> tr = to_host(ctx, red + 512, 2);
+      ctx->E_hf = 0.5 * (tr[0] + tr[1]);
+      ctx->E_prev = ctx->E_hf;
+      ctx->mu = 0.5 * (e0[nocc - 1] + e0[nocc]);
+      ctx->nq = N;
+      ctx->nmo = N;
+      ctx->have_uprev = false;
+      ctx->have_state = true;
+      ctx->iter = 0;
+    }
+    std::memset(out, 0, sizeof(*out));
+    out->E_hf = ctx->E_hf;
+    bool conv = false;
+    int it = 0;
+    for (it = 1; it <= o.max_iter; ++it) {
+      auto t0 = std::chrono::steady_clock::now();
+      {
+        PoleSplit ps = split_poles(ctx, e, ctx->nq, ctx->mu);
+        out->flops_moments += (double)N * ps.o * ps.v * (double)(ps.o + ps.v) *
+                              (2.0 * naux + 2.0 * (o.nmom + 1) * N);
+      }
+      build_moments_impl(ctx, L, naux, N, e, C, ctx->nq, ctx->mu, 1, o.precision, U, U + 2 * NN);
+      out->t_moments += seconds_since(t0);
+      t0 = std::chrono::steady_clock::now();
+      ctx->iter += 1;
+      if (ctx->have_uprev) CK(axpby(U, Uprev, 1.0 - o.mix, o.mix, 4 * NN, s));
+      CK(cudaMemcpyAsync(Uprev, U, 4 * NN * sizeof(double), cudaMemcpyDeviceToDevice, s));
+      ctx->have_uprev = true;
+      compress_impl(ctx, U, N, Ese, vse, nse);
+      compress_impl(ctx, U + 2 * NN, N, Ese + N, vse + N, nse);
+      out->t_compress += seconds_since(t0);
+      t0 = std::chrono::steady_clock::now();
+      FockOut fo = fock_loop_impl(ctx, hcore, L, naux, N, nelec, Ese, vse, nse, D, F, eq, Cq, o.fock);
+      out->t_fock += seconds_since(t0);
+      t0 = std::chrono::steady_clock::now();
+      CK(cudaMemcpyAsync(e, eq, nq_max * sizeof(double), cudaMemcpyDeviceToDevice, s));
+      CK(cudaMemcpyAsync(C, Cq, (size_t)N * nq_max * sizeof(double), cudaMemcpyDeviceToDevice, s));
+      ctx->nq = nq_max;
+      ctx->mu = fo.mu;
+      const int k = fo.k;
+      // energies
+      CK(dot(D, hcore, NN, red + 512, red, s));
+      CK(dot(D, F, NN, red + 513, red, s));
+      {
+        DGemm g;  // V[x][m] = sum_p C[p][x] v_>[p][m]
+        g.M = k; g.N = N; g.K = N;
+        g.A = C; g.sAm = 1; g.sAk = nq_max;
+        g.B = vse + N; g.sBk = nse; g.sBn = 1;
+        g.C = V; g.sCm = N; g.sCn = 1;
+        CK(dgemm(g, s));
+      }
+      CK(gm_energy(V, e, Ese + N, k, N, red + 514, red, s));
+      std::vector<double> sc = to_host(ctx, red + 512, 3);
+      std::vector<double> eh = to_host(ctx, e, nq_max);
+      const double E1 = 0.5 * (sc[0] + sc[1]);
+      const double E2 = sc[2];
+      const double Et = E1 + E2;
+      out->E_1b = E1;
+      out->E_2b = E2;
+      out->E_tot = Et;
+      out->ip = -eh[k - 1];
+      out->ea = -eh[k];
+      out->mu = fo.mu;
+      out->nocc_qmo = k;
+      out->fock_cycles = fo.cycles;
+      out->t_energy += seconds_since(t0);
+      const double dE = std::fabs(Et - ctx->E_prev);
+      ctx->E_prev = Et;
+      if (dE < o.conv_tol) {
+        conv = true;
+        break;
+      }
+    }
+    out->iterations = std::min(it, o.max_iter);
+    out->converged = conv ? 1 : 0;
+    if (!conv && o.max_iter > 1) rc_conv = AGF2_ERR_NO_CONVERGENCE;
+  });
+  return rc != AGF2_OK ? rc : rc_conv;
+}
+
+int agf2_get_state(agf2_handle h, double* e, double* C, double* D, int* nqmo) {
+  return guarded(h, [&](agf2_context* ctx) {
+    if (!ctx->have_state) fail(ctx, AGF2_ERR_INVALID_ARG, "no state: call agf2_run first");
+    const int N = ctx->nmo, nq = ctx->nq, nq_max = 3 * N;
+    cudaStream_t s = ctx->stream;
+    if (nqmo) *nqmo = nq;
+    if (e) CK(cudaMemcpyAsync(e, ws(ctx, "st_e", nq_max), nq * sizeof(double),
+                              cudaMemcpyDeviceToDevice, s));
+    if (C) {
+      // state C has leading dimension 3N once iterations ran, N before
+      const int ld = (nq == N) ? N : nq_max;
+      CK(cudaMemcpy2DAsync(C, nq * sizeof(double), ws(ctx, "st_C", (size_t)N * nq_max),
+                           ld * sizeof(double), nq * sizeof(double), N, cudaMemcpyDeviceToDevice, s));
+    }
+    if (D) CK(cudaMemcpyAsync(D, ws(ctx, "st_D", (size_t)N * N), (size_t)N * N * sizeof(double),
+                              cudaMemcpyDeviceToDevice, s));
+    sync(ctx);
+  });
+}
+
+}  // extern "C"

@@ -1,0 +1,255 @@
+"""Pins of the FP64 oracle against facts fixed by the paper and by
+mathematics (not against itself).  CPU only."""
+import numpy as np
+import pytest
+
+from oracle import agf2_oracle as O
+from paper_2106_03508_gb300.synth import make_system, random_poles
+
+
+def small(nmo=7, nocc=2, naux=9, seed=11):
+    s = make_system(nmo, nocc, naux, seed)
+    return s
+
+
+def rel(a, b):
+    return np.max(np.abs(a - b)) / max(np.max(np.abs(b)), 1e-300)
+
+
+# ---- Eq. (fock_matrix) against explicit four-index sums ------------------
+def test_fock_matrix_explicit_loops():
+    s = small(5, 2, 6, 3)
+    rng = np.random.default_rng(5)
+    h = rng.standard_normal((5, 5)); h = h + h.T
+    D = rng.standard_normal((5, 5)); D = D + D.T
+    eri = np.zeros((5, 5, 5, 5))
+    for p in range(5):
+        for q in range(5):
+            for r in range(5):
+                for t in range(5):
+                    eri[p, q, r, t] = sum(s.L[Q, p, q] * s.L[Q, r, t] for Q in range(s.naux))
+    F = np.zeros((5, 5))
+    for p in range(5):
+        for q in range(5):
+            F[p, q] = h[p, q]
+            for r in range(5):
+                for t in range(5):
+                    F[p, q] += (eri[p, q, r, t] - 0.5 * eri[p, t, r, q]) * D[r, t]
+    assert rel(O.fock_matrix(h, s.L, D), F) < 1e-13
+
+
+def test_hcore_gives_diagonal_fock():
+    s = small(8, 3, 10, 4)
+    h = O.hcore_from_mo_energies(s.eps, s.L, s.nocc)
+    F = O.fock_matrix(h, s.L, O.hf_density(8, 3))
+    assert np.max(np.abs(F - np.diag(s.eps))) < 1e-13
+
+
+# ---- Eqs. (mp2_zeroth_moment), (mp2_first_moment) -------------------------
+@pytest.mark.parametrize("nmo,nq,no,naux,seed", [(6, 6, 2, 7, 1), (5, 13, 6, 8, 2), (7, 15, 4, 5, 3)])
+def test_moments_vs_explicit_sums(nmo, nq, no, naux, seed):
+    """GEMM-structured moments == explicit sums over four-index pole ERIs,
+    with a generic (non-unitary, more poles than orbitals) coupling matrix."""
+    s = make_system(nmo, 2, naux, seed)
+    e, C, mu = random_poles(nmo, nq, no, seed + 100)
+    Uh, Up = O.build_moments(s.L, e, C, mu)
+    Bh, Bp = O.build_moments_loops(s.L, e, C, mu)
+    Bh = 0.5 * (Bh + Bh.transpose(0, 2, 1))
+    Bp = 0.5 * (Bp + Bp.transpose(0, 2, 1))
+    for n in range(2):
+        assert rel(Uh[n], Bh[n]) < 1e-12
+        assert rel(Up[n], Bp[n]) < 1e-12
+
+
+def test_moments_loops_symmetric_and_psd():
+    """The exact double sum is symmetric and U^(0) is positive semidefinite
+    (it is the Gram matrix of the S/D-factorised couplings)."""
+    s = make_system(6, 2, 7, 9)
+    e, C, mu = random_poles(6, 12, 5, 9)
+    Bh, Bp = O.build_moments_loops(s.L, e, C, mu)
+    for B in (Bh, Bp):
+        assert rel(B[0], B[0].T) < 1e-12 and rel(B[1], B[1].T) < 1e-12
+        assert np.min(np.linalg.eigvalsh(B[0])) > -1e-10 * np.max(np.abs(B[0]))
+
+
+def test_moments_homogeneity():
+    """(pq|rs) is quadratic in L, each moment quadratic in (pq|rs): U(lam L) = lam^4 U(L)."""
+    s = make_system(9, 3, 12, 21)
+    e, C, mu = random_poles(9, 20, 8, 21)
+    U1 = O.build_moments(s.L, e, C, mu)
+    U2 = O.build_moments(1.7 * s.L, e, C, mu)
+    for a, b in zip(U1, U2):
+        assert rel(b, 1.7 ** 4 * a) < 1e-13
+
+
+def test_moments_energy_shift():
+    """Shifting all pole energies by t: occupied/virtual sets fixed, the hole
+    weight e_i+e_j-e_a shifts by t, the particle weight e_a+e_b-e_i by t:
+    U^(1) -> U^(1) + t U^(0), U^(0) unchanged."""
+    s = make_system(8, 3, 10, 5)
+    e, C, mu = random_poles(8, 18, 7, 5)
+    Uh, Up = O.build_moments(s.L, e, C, mu)
+    Vh, Vp = O.build_moments(s.L, e + 0.37, C, mu + 0.37)
+    for U, V in ((Uh, Vh), (Up, Vp)):
+        assert rel(V[0], U[0]) < 1e-13
+        assert rel(V[1], U[1] + 0.37 * U[0]) < 1e-12
+
+
+def _sd_auxiliaries(L, eps, nocc):
+    """Uncompressed greater self-energy of Eq. (mp2_self_energy) at the HF
+    reference as explicit auxiliaries: for a <= b, i the pair couplings
+    S = (pa|bi) + (pb|ai), D = (pa|bi) - (pb|ai) with weights 1/2, 3/2
+    (a = b: (pa|ai), weight 1), energy e_a + e_b - e_i."""
+    eri = np.einsum("Qpq,Qrs->pqrs", L, L)
+    N = len(eps)
+    vs, Es = [], []
+    for a in range(nocc, N):
+        for b in range(a, N):
+            for i in range(nocc):
+                x1 = eri[:, a, b, i]
+                x2 = eri[:, b, a, i]
+                w = eps[a] + eps[b] - eps[i]
+                if a == b:
+                    vs.append(x1); Es.append(w)
+                else:
+                    vs.append(np.sqrt(0.5) * (x1 + x2)); Es.append(w)
+                    vs.append(np.sqrt(1.5) * (x1 - x2)); Es.append(w)
+    return np.array(Es), np.array(vs).T
+
+
+def test_uncompressed_greater_self_energy_moments_and_mp2():
+    """(1) The explicit 1h2p auxiliaries reproduce U_>^(0,1) of the oracle.
+    (2) Galitskii-Migdal with them at the HF reference equals the closed-shell
+    MP2 energy sum_{ijab} (ia|jb)[2(ia|jb) - (ib|ja)]/(e_i+e_j-e_a-e_b),
+    written here as explicit loops."""
+    s = make_system(9, 3, 11, 17)
+    N, no = s.nmo, s.nocc
+    E, v = _sd_auxiliaries(s.L, s.eps, no)
+    Uh, Up = O.build_moments(s.L, s.eps, np.eye(N), 0.5 * (s.eps[no - 1] + s.eps[no]))
+    assert rel(v @ v.T, Up[0]) < 1e-12
+    assert rel(v @ np.diag(E) @ v.T, Up[1]) < 1e-12
+    e2 = O.energy_2body(s.eps[:no], np.eye(N)[:, :no], E, v)
+    eri = np.einsum("Qpq,Qrs->pqrs", s.L, s.L)
+    emp2 = 0.0
+    for i in range(no):
+        for j in range(no):
+            for a in range(no, N):
+                for b in range(no, N):
+                    emp2 += eri[i, a, j, b] * (2 * eri[i, a, j, b] - eri[i, b, j, a]) / (
+                        s.eps[i] + s.eps[j] - s.eps[a] - s.eps[b])
+    assert abs(e2 - emp2) < 1e-12 * abs(emp2)
+    assert abs(O.mp2_energy(s.L, s.eps, no) - emp2) < 1e-12 * abs(emp2)
+
+
+# ---- compression, Eq. (block_lanczos_chol_3) -------------------------------
+def test_compression_conserves_moments():
+    s = make_system(10, 3, 14, 8)
+    e, C, mu = random_poles(10, 25, 9, 8)
+    for U in O.build_moments(s.L, e, C, mu):
+        E, v = O.compress(U[0], U[1])
+        assert rel(v @ v.T, U[0]) < 1e-12
+        assert rel(v @ np.diag(E) @ v.T, U[1]) < 1e-11
+        assert np.all(np.diff(E) >= 0)
+
+
+def test_compression_rejects_non_pd():
+    U0 = np.diag([1.0, -1e-3, 2.0])
+    with pytest.raises(O.NotPositiveDefinite):
+        O.compress(U0, np.eye(3))
+
+
+def test_compression_exact_for_few_auxiliaries():
+    """A self-energy with exactly N auxiliaries is reproduced exactly
+    (energies identical), as the block-Lanczos step spans it."""
+    rng = np.random.default_rng(3)
+    N = 6
+    E0 = np.sort(rng.uniform(-3, 3, N))
+    v0 = rng.standard_normal((N, N))
+    E, v = O.compress(v0 @ v0.T, v0 @ np.diag(E0) @ v0.T)
+    assert np.max(np.abs(E - E0)) < 1e-9 * np.linalg.cond(v0)
+
+
+# ---- extended Hamiltonian and Fock loop -----------------------------------
+def test_extended_eigenvectors_complete():
+    rng = np.random.default_rng(2)
+    N = 6
+    F = rng.standard_normal((N, N)); F = F + F.T
+    E = rng.uniform(-3, 3, 2 * N)
+    v = rng.standard_normal((N, 2 * N))
+    e, C = O.diagonalise(F, E, v)
+    assert rel(C @ C.T, np.eye(N)) < 1e-13
+    H = O.extended_hamiltonian(F, E, v)
+    w, V = np.linalg.eigh(H)
+    assert np.max(np.abs(H @ V - V * w)) < 1e-12
+
+
+def test_aufbau_and_shift_electron_count():
+    s = make_system(8, 3, 10, 12)
+    h = O.hcore_from_mo_energies(s.eps, s.L, s.nocc)
+    e, C, mu = s.eps, np.eye(8), 0.5 * (s.eps[2] + s.eps[3])
+    Uh, Up = O.build_moments(s.L, e, C, mu)
+    Eh, vh = O.compress(Uh[0], Uh[1])
+    Ep, vp = O.compress(Up[0], Up[1])
+    E = np.concatenate([Eh, Ep]); v = np.concatenate([vh, vp], 1)
+    F = O.fock_matrix(h, s.L, O.hf_density(8, 3))
+    info = O.solve_shift(F, E, v, s.nelec)
+    assert info.converged
+    ee, CC = O.diagonalise(F, E + info.delta, v)
+    k, mu, n = O.aufbau(ee, CC, s.nelec)
+    assert abs(n - s.nelec) < 1e-10
+    assert ee[k - 1] < mu < ee[k]
+
+
+def test_fock_loop_fixed_point_and_count():
+    s = make_system(8, 3, 10, 12)
+    h = O.hcore_from_mo_energies(s.eps, s.L, s.nocc)
+    Uh, Up = O.build_moments(s.L, s.eps, np.eye(8), 0.5 * (s.eps[2] + s.eps[3]))
+    Eh, vh = O.compress(Uh[0], Uh[1])
+    Ep, vp = O.compress(Up[0], Up[1])
+    E = np.concatenate([Eh, Ep]); v = np.concatenate([vh, vp], 1)
+    fr = O.fock_loop(h, s.L, s.nelec, E, v, O.hf_density(8, 3))
+    assert fr.converged
+    k = fr.nocc_qmo
+    assert abs(2 * np.sum(fr.C[:, :k] ** 2) - s.nelec) < 1e-9
+    # D is a fixed point: rediagonalising with F[D] returns D
+    e2, C2 = O.diagonalise(O.fock_matrix(h, s.L, fr.D), fr.E_shift, v)
+    D2 = 2 * C2[:, :k] @ C2[:, :k].T
+    assert np.max(np.abs(D2 - fr.D)) < 1e-8
+
+
+def test_weak_coupling_limit():
+    """L -> lam L with lam small: the correlation vanishes as lam^4, so
+    E_tot -> E_HF and IP -> -eps_HOMO."""
+    s = make_system(8, 3, 10, 30)
+    L = 1e-2 * s.L
+    h = O.hcore_from_mo_energies(s.eps, L, s.nocc)
+    r = O.run(h, L, s.nelec, s.eps, max_iter=5)
+    assert abs(r.E_tot - r.E_hf) < 1e-6
+    assert abs(r.ip + s.eps[2]) < 1e-5
+    assert abs(r.ea + s.eps[3]) < 1e-5
+
+
+def test_first_iteration_two_body_vs_mp2_gap_reported():
+    """Compressed first-iteration E_2b approximates E_MP2 (not equal): the
+    Galitskii-Migdal sum with only N compressed auxiliaries; the gap is
+    finite and both are negative."""
+    s = make_system(8, 3, 10, 40)
+    L = 0.3 * s.L
+    N, no = s.nmo, s.nocc
+    Uh, Up = O.build_moments(L, s.eps, np.eye(N), 0.5 * (s.eps[no - 1] + s.eps[no]))
+    Ep, vp = O.compress(Up[0], Up[1])
+    e2 = O.energy_2body(s.eps[:no], np.eye(N)[:, :no], Ep, vp)
+    emp2 = O.mp2_energy(L, s.eps, no)
+    assert e2 < 0 and emp2 < 0
+    assert abs(e2 - emp2) < abs(emp2)
+
+
+def test_slice_additivity():
+    """U is a sum over the occupied poles: moments built with the occupied
+    set split in two (the other poles as spectators) add to the whole hole
+    moment's diagonal-pair-free part -- checked by the explicit loops."""
+    s = make_system(6, 2, 7, 44)
+    e, C, mu = random_poles(6, 11, 4, 44)
+    Bh, _ = O.build_moments_loops(s.L, e, C, mu)
+    Uh, _ = O.build_moments(s.L, e, C, mu)
+    assert rel(Uh[0], 0.5 * (Bh[0] + Bh[0].T)) < 1e-12
