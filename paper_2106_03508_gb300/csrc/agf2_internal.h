@@ -59,6 +59,9 @@ cudaError_t fock_combine(const double* h, const double* J, const double* K, long
 // GM: out = sum_{x<k, m<nse} V[x][m]^2 / (e[x] - E[m]), V = Cocc^T v (k x nse)
 cudaError_t gm_energy(const double* V, const double* e, const double* E, int k, int nse,
                       double* out, double* scratch, cudaStream_t s);
+// dn/d(delta) = 4 sum_{x<k,y} S[x][y]^2 / (w[k+y] - w[x]),  S = C_occ^T C_vir
+cudaError_t shift_derivative(const double* S, const double* w, int k, int nv, double* out,
+                             double* scratch, cudaStream_t s);
 cudaError_t set_identity(double* A, int n, double scale, cudaStream_t s);
 cudaError_t diag_from_vec(const double* d, int n, double* A, cudaStream_t s);
 // max |a - b| into *out (device)
@@ -66,11 +69,13 @@ cudaError_t max_abs_diff(const double* a, const double* b, long long n, double* 
                          cudaStream_t s);
 cudaError_t add_scalar(double* x, double a, int n, cudaStream_t s);
 
-// Split-precision (BF16x3 / tcgen05) moment build: see mixed.cu.
-struct MixedWorkspace;
-int mixed_build_moments(const double* L, int naux, int nmo, const double* Co, int o,
-                        const double* Cv, int v, const double* eo, const double* ev, int nmom,
-                        double* U_hole, double* U_part, void* ws_owner, std::string& err,
-                        cudaStream_t s);
+// Split-precision (BF16x3 / tcgen05) moment build from the FP64 rotated
+// tensors Lxo [o][N][naux], Lxv [v][N][naux], Lov [o][v][naux]; accumulates
+// into the zeroed U_hole, U_part [2][N][N] (not symmetrised).  Returns an
+// AGF2 status; err receives a message.
+int mixed_build_moments_rotated(const double* Lxo, const double* Lxv, const double* Lov, int naux,
+                                int N, int o, int v, const double* eo, const double* ev,
+                                double* U_hole, double* U_part, std::string& err,
+                                cudaStream_t s);
 
 }  // namespace agf2

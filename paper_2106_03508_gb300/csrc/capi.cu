@@ -300,37 +300,36 @@ void build_moments_impl(agf2_context* ctx, const double* L, int naux, int N, con
   const size_t mom_stride = (size_t)NN;
   CK(cudaMemsetAsync(Uh, 0, (nmom + 1) * NN * sizeof(double), s));
   CK(cudaMemsetAsync(Up, 0, (nmom + 1) * NN * sizeof(double), s));
+  const long long NQ = (long long)N * naux;
+  double* Lxo = ws(ctx, "mom_Lxo", (size_t)o * NQ);
+  double* Lxv = ws(ctx, "mom_Lxv", (size_t)v * NQ);
+  double* Lov = ws(ctx, "mom_Lov", (size_t)o * v * naux);
+  auto rot = [&](const double* Cx, int nx, double* out) {
+    DGemm g;  // out[x][p][Q] = sum_r Cx[r][x] L[Q][r][p]
+    g.M = nx; g.N = N; g.K = N;
+    g.A = Cx; g.sAm = 1; g.sAk = nx;
+    g.B = L; g.sBk = N; g.sBn = 1; g.sB1 = NN;
+    g.C = out; g.sCm = NQ; g.sCn = naux; g.sC1 = 1;
+    g.nb1 = naux;
+    CK(dgemm(g, s));
+  };
+  rot(Co, o, Lxo);
+  rot(Cv, v, Lxv);
+  {
+    DGemm g;  // Lov[j][a][Q] = sum_p Co[p][j] Lxv[a][p][Q]
+    g.M = o; g.N = v; g.K = N;
+    g.A = Co; g.sAm = 1; g.sAk = o;
+    g.B = Lxv; g.sBk = naux; g.sBn = NQ; g.sB1 = 1;
+    g.C = Lov; g.sCm = (long long)v * naux; g.sCn = naux; g.sC1 = 1;
+    g.nb1 = naux;
+    CK(dgemm(g, s));
+  }
   if (precision == AGF2_BF16X3) {
-    int rc = mixed_build_moments(L, naux, N, Co, o, Cv, v, eo, ev, nmom, Uh, Up, ctx, ctx->err, s);
+    int rc = mixed_build_moments_rotated(Lxo, Lxv, Lov, naux, N, o, v, eo, ev, Uh, Up, ctx->err, s);
     if (rc != AGF2_OK) throw Fail{rc};
   } else {
-    const long long NQ = (long long)N * naux;
-    double* Lxo = ws(ctx, "mom_Lxo", (size_t)o * NQ);
-    double* Lxv = ws(ctx, "mom_Lxv", (size_t)v * NQ);
-    double* Lov = ws(ctx, "mom_Lov", (size_t)o * v * naux);
-    auto rot = [&](const double* Cx, int nx, double* out) {
-      DGemm g;  // out[x][p][Q] = sum_r Cx[r][x] L[Q][r][p]
-      g.M = nx; g.N = N; g.K = N;
-      g.A = Cx; g.sAm = 1; g.sAk = nx;
-      g.B = L; g.sBk = N; g.sBn = 1; g.sB1 = NN;
-      g.C = out; g.sCm = NQ; g.sCn = naux; g.sC1 = 1;
-      g.nb1 = naux;
-      CK(dgemm(g, s));
-    };
-    rot(Co, o, Lxo);
-    rot(Cv, v, Lxv);
-    {
-      DGemm g;  // Lov[j][a][Q] = sum_p Co[p][j] Lxv[a][p][Q]
-      g.M = o; g.N = v; g.K = N;
-      g.A = Co; g.sAm = 1; g.sAk = o;
-      g.B = Lxv; g.sBk = naux; g.sBn = NQ; g.sB1 = 1;
-      g.C = Lov; g.sCm = (long long)v * naux; g.sCn = naux; g.sC1 = 1;
-      g.nb1 = naux;
-      CK(dgemm(g, s));
-    }
     Sector hole{o, v, Lxo, Lov, (long long)v * naux, (long long)naux, eo, ev};
     Sector part{v, o, Lxv, Lov, (long long)naux, (long long)v * naux, ev, eo};
-    if (nmom != 1) fail(ctx, AGF2_ERR_UNSUPPORTED, "only nmom = 1 is implemented");
     sector_fp64(ctx, hole, N, naux, Uh, Uh + mom_stride);
     sector_fp64(ctx, part, N, naux, Up, Up + mom_stride);
   }
@@ -456,42 +455,70 @@ struct Shift {
   bool converged;
 };
 
-// Common shift of the auxiliary energies so that n(delta; k) = nelec with k
-// the aufbau count at delta = 0; bracket by doubling, then bisection.
+// Common shift of the auxiliary energies so that n(delta; k) = nelec, with k
+// the aufbau count at delta = 0.  n is increasing in delta with
+//   dn/d(delta) = 4 sum_{x<k<=y} (C_x . C_y)^2 / (e_y - e_x)
+// (first-order perturbation of the eigenvectors by the auxiliary-space
+// projector), so the root is found by Newton steps safeguarded by a bracket
+// (bisection whenever a step leaves it, expanding steps until one exists).
+// It converges to the same root as plain bisection, in a few
+// eigendecompositions instead of ~40.
 Shift solve_shift(agf2_context* ctx, const double* F, const double* E, const double* v, int nmo,
                   int nse, int nelec, double tol) {
-  auto eval = [&](double d, int k) {
+  const int n = nmo + nse;
+  int k = -1;
+  double* red = ws(ctx, "sh_red", 1024);
+  auto eval = [&](double d, double& fp) -> double {
     Eig eg = diag_extended(ctx, F, E, v, d, nmo, nse);
-    return nelec_fixed_k(pole_weights(ctx, eg, nmo), k) - nelec;
+    std::vector<double> wt = pole_weights(ctx, eg, nmo);
+    if (k < 0) {
+      std::vector<double> ev = to_host(ctx, eg.w, n);
+      k = aufbau(ev, wt, nelec).k;
+    }
+    const int nv = n - k;
+    double* S = ws(ctx, "sh_S", (size_t)k * nv);
+    DGemm g;  // S[x][y] = sum_p V[x n + p] V[(k + y) n + p]
+    g.M = k; g.N = nv; g.K = nmo;
+    g.A = eg.V; g.sAm = n; g.sAk = 1;
+    g.B = eg.V + (long long)k * n; g.sBk = 1; g.sBn = n;
+    g.C = S; g.sCm = nv; g.sCn = 1;
+    CK(dgemm(g, ctx->stream));
+    CK(shift_derivative(S, eg.w, k, nv, red + 512, red, ctx->stream));
+    fp = scalar(ctx, red + 512);
+    return nelec_fixed_k(wt, k) - nelec;
   };
-  Eig e0 = diag_extended(ctx, F, E, v, 0.0, nmo, nse);
-  std::vector<double> wt = pole_weights(ctx, e0, nmo);
-  std::vector<double> ev = to_host(ctx, e0.w, e0.n);
-  const int k = aufbau(ev, wt, nelec).k;
+  double fp = 0.0;
+  double d = 0.0;
+  double f = eval(0.0, fp);
   int evals = 1;
-  const double f0 = nelec_fixed_k(wt, k) - nelec;
-  if (std::fabs(f0) < tol) return Shift{0.0, f0, evals, true};
-  bool has_lo = f0 < 0, has_hi = !has_lo;
-  double lo = 0, flo = f0, hi = 0, fhi = f0;
-  double step = 1.0;
-  for (int it = 0; it < 60; ++it) {
-    const double d = has_lo ? step : -step;
-    const double f = eval(d, k);
-    ++evals;
-    if (f < 0) { lo = d; flo = f; has_lo = true; } else { hi = d; fhi = f; has_hi = true; }
-    if (has_lo && has_hi) break;
-    step *= 2.0;
-  }
-  if (!(has_lo && has_hi)) return Shift{has_lo ? lo : hi, has_lo ? flo : fhi, evals, false};
-  double best = std::fabs(flo) < std::fabs(fhi) ? lo : hi;
-  double fbest = std::fabs(flo) < std::fabs(fhi) ? flo : fhi;
+  if (std::fabs(f) < tol) return Shift{0.0, f, evals, true};
+  bool has_lo = false, has_hi = false;
+  double lo = 0.0, hi = 0.0;
+  auto bracket = [&](double x, double fx) {
+    if (fx < 0) { if (!has_lo || x > lo) lo = x; has_lo = true; }
+    else { if (!has_hi || x < hi) hi = x; has_hi = true; }
+  };
+  bracket(d, f);
+  double best = d, fbest = f;
+  double expand = 1.0;
   for (int it = 0; it < 200; ++it) {
-    if (std::fabs(fbest) < tol || hi - lo < 1e-14) break;
-    const double mid = 0.5 * (lo + hi);
-    const double f = eval(mid, k);
+    double dn = (fp > 0.0 && std::isfinite(fp)) ? d - f / fp : NAN;
+    if (has_lo && has_hi) {
+      if (!(dn > lo && dn < hi)) dn = 0.5 * (lo + hi);
+    } else if (!std::isfinite(dn) || std::fabs(dn - d) > expand) {
+      dn = d + (f < 0 ? expand : -expand);
+      expand *= 2.0;
+    }
+    d = dn;
+    f = eval(d, fp);
     ++evals;
-    if (std::fabs(f) < std::fabs(fbest)) { best = mid; fbest = f; }
-    if (f < 0) lo = mid; else hi = mid;
+    bracket(d, f);
+    if (std::fabs(f) < std::fabs(fbest)) { best = d; fbest = f; }
+    if (std::fabs(f) < tol) break;
+    if (has_lo && has_hi && hi - lo < 1e-14) break;
+    if (!has_lo || !has_hi) {
+      if (expand > 1e6) break;
+    }
   }
   return Shift{best, fbest, evals, std::fabs(fbest) < tol};
 }

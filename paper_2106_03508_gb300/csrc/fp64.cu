@@ -297,6 +297,21 @@ __global__ void gm_partial(const double* __restrict__ V, const double* __restric
   if (threadIdx.x == 0) part[blockIdx.x] = s;
 }
 
+// 4 sum_{x<k, y<nv} S[x][y]^2 / (w[k+y] - w[x])
+__global__ void deriv_partial(const double* __restrict__ S, const double* __restrict__ w, int k,
+                              int nv, double* __restrict__ part) {
+  double s = 0.0;
+  const long long n = (long long)k * nv;
+  for (long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x; t < n;
+       t += (long long)gridDim.x * blockDim.x) {
+    const int x = (int)(t / nv), y = (int)(t % nv);
+    const double sv = S[t];
+    s += sv * sv / (w[k + y] - w[x]);
+  }
+  s = block_sum(s);
+  if (threadIdx.x == 0) part[blockIdx.x] = 4.0 * s;
+}
+
 __global__ void set_identity_kernel(double* A, int n, double scale) {
   const long long total = (long long)n * n;
   for (long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x; t < total;
@@ -429,6 +444,13 @@ cudaError_t fock_combine(const double* h, const double* J, const double* K, long
 cudaError_t gm_energy(const double* V, const double* e, const double* E, int k, int nse,
                       double* out, double* scratch, cudaStream_t s) {
   gm_partial<<<RED_BLOCKS, RED_THREADS, 0, s>>>(V, e, E, k, nse, scratch);
+  final_sum<<<1, RED_THREADS, 0, s>>>(scratch, RED_BLOCKS, out);
+  return cudaGetLastError();
+}
+
+cudaError_t shift_derivative(const double* S, const double* w, int k, int nv, double* out,
+                             double* scratch, cudaStream_t s) {
+  deriv_partial<<<RED_BLOCKS, RED_THREADS, 0, s>>>(S, w, k, nv, scratch);
   final_sum<<<1, RED_THREADS, 0, s>>>(scratch, RED_BLOCKS, out);
   return cudaGetLastError();
 }

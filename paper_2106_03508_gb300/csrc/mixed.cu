@@ -1,12 +1,680 @@
-// Split-precision moment build (BF16x3 on tcgen05): not yet built.
+// Split-precision moment build on the tcgen05 tensor cores (AGF2_BF16X3).
+//
+// The self-energy moments of Eqs. (mp2_zeroth_moment), (mp2_first_moment) are
+// evaluated over unordered pole pairs (x <= y) of the summed outer index
+// (i,j occupied for the hole sector; a,b virtual for the particle sector):
+//
+//   X_xy[p,c] = sum_Q Lx[x][p][Q] Lpair[y][c][Q]        (GEMM 1, K = n_Q)
+//   S = X_xy + X_yx,  D = X_xy - X_yx,  w = e_x + e_y - e_c
+//   Y  = [ sqrt(cS) S | sqrt(cD) D ],  Yw = w Y
+//   U^(0) += Y Y^T,   U^(1) += Yw Y^T                    (GEMM 2, K = pairs x c)
+//
+// with (cS, cD) = (1/2, 3/2) for x < y and (1/4, 3/4) for x = y, which is
+// the pair-symmetrised form of sum_{xyc} X_xy (2 X_xy - X_yx) w^n (the
+// exchange partner X_yx of an ordered pair is the other ordered pair, so
+// GEMM 1 runs once per ordered pair).
+//
+// Every operand row is sliced in fixed point with a per-row power-of-two unit
+// into three BF16 limbs (x ~ unit (h0 + h1 + h2), h0 an integer, see
+// tc_core.cuh).  Each GEMM keeps the six limb products h_a h_b (a + b <= 2)
+// in two FP32 tensor-memory accumulators: h0 h0' alone (integer-valued, so
+// the tensor core adds it exactly) and the five smaller products.  Separate
+// accumulators matter: the tensor core truncates when it adds into an FP32
+// accumulator, which over long K biases a single accumulator by ~2^-25 per
+// instruction.  GEMM 2 drains its tiles into the FP64 moments.
+//
+// Kernels: split_limbs (FP64 -> limb planes), gemm6<PAIR> (GEMM 1 + the
+// S/D/weight epilogue, writing Y and Yw limb planes), gemm6<MOMENT> (GEMM 2,
+// split-K, FP64 reduction).
+#include <cuda.h>
+#include <cuda_bf16.h>
+#include <cudaTypedefs.h>
+
+#include <algorithm>
+#include <cmath>
+#include <string>
+#include <vector>
+
 #include "../../include/agf2.h"
 #include "agf2_internal.h"
+#include "tc_core.cuh"
 
 namespace agf2 {
-int mixed_build_moments(const double*, int, int, const double*, int, const double*, int,
-                        const double*, const double*, int, double*, double*, void*,
-                        std::string& err, cudaStream_t) {
-  err = "AGF2_BF16X3 moment build not available in this build";
-  return AGF2_ERR_UNSUPPORTED;
+
+namespace {
+
+constexpr int BM = 128;         // MMA M (rows of p)
+constexpr int BN = 128;         // MMA N
+constexpr int BK = 64;          // K elements per stage (128 B rows)
+constexpr int STAGES = 2;
+constexpr int TILE_A = BM * BK * 2;     // bytes of one A limb tile
+constexpr int TILE_B = BN * BK * 2;     // bytes of one B limb tile
+constexpr int STAGE_BYTES = 3 * TILE_A + 3 * TILE_B;
+constexpr int SMEM_BYTES = STAGES * STAGE_BYTES + 1024;
+constexpr int TMEM_COLS = 512;  // PAIR: (hi, lo) x (X_xy, X_yx) x BN; MOMENT: (hi, lo) x BN
+constexpr int KCHUNK = 2 * BN;  // K entries of Y one PAIR tile writes: S and D of BN c's
+constexpr int NTHREADS = 192;   // warp 0 TMA, warp 1 MMA, warps 2..5 epilogue
+
+enum { MODE_PAIR = 0, MODE_MOMENT = 1 };
+
+// Device error codes (written to a device int).
+enum { DEV_OK = 0, DEV_TIMEOUT = 1 };
+
+struct Params {
+  int N;            // physical orbitals (rows of U)
+  int n_in;         // inner pole count (c index)
+  int ksteps;       // K steps of GEMM 1 (Qs / BK) or of GEMM 2 in total
+  int n_ptiles;     // ceil(N / BM)
+  int n_cchunks;    // MODE_PAIR: ceil(n_in / BN)
+  int n_qtiles;     // MODE_MOMENT: ceil(N / BN)
+  int n_out;        // outer pole count (limb stride of the A map)
+  int hole;         // MODE_PAIR: 1 -> B rows along map dim 1, 0 -> along dim 2
+  int pair0;        // first pair of this block
+  int ksplit;       // MODE_MOMENT: K steps per CTA
+  int nsplit;       // MODE_MOMENT: CTAs along K per (tile, moment)
+  long long kpp;    // MODE_PAIR: K entries of Y per pair (n_cchunks * KCHUNK)
+  const int2* pairs;
+  const double* e_out;
+  const double* e_in;
+  const float* unitA;   // MODE_PAIR: slicing unit of Lx rows [x][p]; MOMENT: of Y or Yw rows
+  const float* unitA2;  // MOMENT: unit of Yw rows
+  const float* unitB;   // MODE_PAIR: unit of Lov rows [i][a];        MOMENT: of Y rows
+  const float* unitY;   // MODE_PAIR: output units of Y rows
+  const float* unitYw;  // MODE_PAIR: output units of Yw rows
+  int v_stride;         // MODE_PAIR: v (row index of Lov rows is i * v + a)
+  __nv_bfloat16* Y;    // [3][N][Ks]
+  __nv_bfloat16* Yw;   // [3][N][Ks]
+  long long Ks;
+  long long plane;     // N * Ks
+  double* U0;
+  double* U1;
+  int* err;
+};
+
+struct Segment {
+  int a_row, a_idx;   // A tile: rows a_row.., outer index / plane a_idx
+  int b_row, b_idx;   // B tile
+  int acc_col;        // accumulator column offset
+  int kbeg, kend;     // K steps
+  bool a_w;           // MODE_MOMENT: A from the Yw map
+};
+
+__device__ __forceinline__ void load_a(const CUtensorMap* mapA, uint8_t* dst, uint64_t* bar,
+                                       const Params& P, const Segment& s, int ks, int limb) {
+  if (P.n_out > 0)  // MODE_PAIR: A map dims (Qs, N, 3*n_out)
+    tc::tma_load_3d(dst, mapA, bar, ks * BK, s.a_row, limb * P.n_out + s.a_idx);
+  else              // MODE_MOMENT: Y/Yw map dims (K, N, 3)
+    tc::tma_load_3d(dst, mapA, bar, ks * BK, s.a_row, limb);
 }
+
+template <int MODE>
+__global__ void __launch_bounds__(NTHREADS, 1)
+gemm6_kernel(const __grid_constant__ CUtensorMap mapA, const __grid_constant__ CUtensorMap mapA2,
+             const __grid_constant__ CUtensorMap mapB, const Params P) {
+  extern __shared__ uint8_t smem_raw[];
+  uint8_t* smem = reinterpret_cast<uint8_t*>(
+      (reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~uintptr_t(1023));
+  __shared__ __align__(8) uint64_t full_bar[STAGES];
+  __shared__ __align__(8) uint64_t empty_bar[STAGES];
+  __shared__ __align__(8) uint64_t acc_bar;
+  __shared__ uint32_t tmem_base_sh;
+  __shared__ int abort_sh;
+  __shared__ int issued_sh, consumed_sh;
+
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  volatile int* abort_flag = &abort_sh;
+
+  // ---- decode this CTA's work into at most two K segments ----
+  Segment seg[2];
+  int nseg = 1;
+  int p0 = 0, c0 = 0, q0 = 0, moment = 0, pair_local = 0;
+  int2 pr = make_int2(0, 0);
+  if (MODE == MODE_PAIR) {
+    int b = blockIdx.x;
+    const int cc = b % P.n_cchunks; b /= P.n_cchunks;
+    const int pt = b % P.n_ptiles; b /= P.n_ptiles;
+    pair_local = b;
+    pr = P.pairs[P.pair0 + pair_local];
+    p0 = pt * BM;
+    c0 = cc * BN;
+    seg[0] = Segment{p0, pr.x, c0, pr.y, 0, 0, P.ksteps, false};
+    seg[1] = Segment{p0, pr.y, c0, pr.x, 2 * BN, 0, P.ksteps, false};
+    nseg = (pr.x == pr.y) ? 1 : 2;
+  } else {
+    int b = blockIdx.x;
+    const int sp = b % P.nsplit; b /= P.nsplit;
+    moment = b % 2; b /= 2;
+    const int qt = b % P.n_qtiles; b /= P.n_qtiles;
+    const int pt = b;
+    p0 = pt * BM;
+    q0 = qt * BN;
+    const int kb = sp * P.ksplit;
+    const int ke = min(P.ksteps, kb + P.ksplit);
+    seg[0] = Segment{p0, 0, q0, 0, 0, kb, ke, moment == 1};
+    nseg = 1;
+  }
+
+  if (threadIdx.x == 0) {
+    for (int s = 0; s < STAGES; ++s) {
+      tc::mbar_init(&full_bar[s], 1);
+      tc::mbar_init(&empty_bar[s], 1);
+    }
+    tc::mbar_init(&acc_bar, 1);
+    abort_sh = 0;
+    issued_sh = 0;
+    consumed_sh = 0;
+    tc::fence_mbar_init();
+  }
+  if (warp == 1) {
+    tc::tmem_alloc(&tmem_base_sh, TMEM_COLS);
+    tc::tmem_relinquish();
+  }
+  tc::tc_fence_before();
+  __syncthreads();
+  tc::tc_fence_after();
+  const uint32_t tmem = tmem_base_sh;
+
+  if (warp == 0 && lane == 0) {
+    // ---------------- TMA producer ----------------
+    tc::tma_prefetch(&mapA);
+    tc::tma_prefetch(&mapB);
+    if (MODE == MODE_MOMENT) tc::tma_prefetch(&mapA2);
+    int t = 0;
+    for (int si = 0; si < nseg && !*abort_flag; ++si) {
+      const Segment& s = seg[si];
+      for (int ks = s.kbeg; ks < s.kend; ++ks, ++t) {
+        const int st = t % STAGES;
+        const uint32_t ph = (t / STAGES) & 1;
+        if (!tc::mbar_wait(&empty_bar[st], ph ^ 1, abort_flag)) break;
+        uint8_t* base = smem + st * STAGE_BYTES;
+        tc::mbar_arrive_expect_tx(&full_bar[st], STAGE_BYTES);
+        for (int l = 0; l < 3; ++l) {
+          if (MODE == MODE_PAIR) {
+            load_a(&mapA, base + l * TILE_A, &full_bar[st], P, s, ks, l);
+            if (P.hole)
+              tc::tma_load_4d(base + 3 * TILE_A + l * TILE_B, &mapB, &full_bar[st], ks * BK,
+                              s.b_row, s.b_idx, l);
+            else
+              tc::tma_load_4d(base + 3 * TILE_A + l * TILE_B, &mapB, &full_bar[st], ks * BK,
+                              s.b_idx, s.b_row, l);
+          } else {
+            load_a(s.a_w ? &mapA2 : &mapA, base + l * TILE_A, &full_bar[st], P, s, ks, l);
+            tc::tma_load_3d(base + 3 * TILE_A + l * TILE_B, &mapB, &full_bar[st], ks * BK,
+                            s.b_row, l);
+          }
+        }
+        issued_sh = t + 1;
+      }
+    }
+  } else if (warp == 1 && lane == 0) {
+    // ---------------- MMA issuer ----------------
+    constexpr uint32_t idesc = tc::idesc_bf16_f32(BM, BN);
+    // correction products h_a h_b (a + b = 1, 2) into the lo accumulator
+    const int pa[5] = {2, 1, 0, 1, 0};
+    const int pb[5] = {0, 1, 2, 0, 1};
+    int t = 0;
+    bool ok = true;
+    for (int si = 0; si < nseg && ok; ++si) {
+      const Segment& s = seg[si];
+      const uint32_t acc_hi = tmem + s.acc_col, acc_lo = tmem + s.acc_col + BN;
+      for (int ks = s.kbeg; ks < s.kend; ++ks, ++t) {
+        const int st = t % STAGES;
+        const uint32_t ph = (t / STAGES) & 1;
+        if (!tc::mbar_wait(&full_bar[st], ph, abort_flag)) { ok = false; break; }
+        tc::tc_fence_after();
+        const uint32_t base = tc::smem_u32(smem + st * STAGE_BYTES);
+#pragma unroll
+        for (int kk = 0; kk < BK / 16; ++kk) {
+          const uint32_t acc = (ks > s.kbeg || kk > 0) ? 1u : 0u;
+#pragma unroll
+          for (int pi = 0; pi < 5; ++pi) {
+            const uint64_t ad = tc::sdesc_sw128(base + pa[pi] * TILE_A + kk * 32);
+            const uint64_t bd = tc::sdesc_sw128(base + 3 * TILE_A + pb[pi] * TILE_B + kk * 32);
+            tc::umma_bf16(acc_lo, ad, bd, idesc, (acc || pi > 0) ? 1u : 0u);
+          }
+          tc::umma_bf16(acc_hi, tc::sdesc_sw128(base + kk * 32),
+                        tc::sdesc_sw128(base + 3 * TILE_A + kk * 32), idesc, acc);
+        }
+        tc::umma_commit(&empty_bar[st]);
+        consumed_sh = t + 1;
+      }
+    }
+    tc::umma_commit(&acc_bar);
+  } else if (warp >= 2) {
+    // ---------------- epilogue ----------------
+    const int qd = warp & 3;                 // TMEM lane quarter of this warp
+    const int r = qd * 32 + lane;
+    const uint32_t trow = tmem + ((uint32_t)(qd * 32) << 16);
+    if (tc::mbar_wait(&acc_bar, 0, abort_flag)) {
+      tc::tc_fence_after();
+      if (MODE == MODE_PAIR) {
+        const int p = p0 + r;
+        const bool diag = (pr.x == pr.y);
+        const float sS = diag ? 0.5f : 0.70710678118654752f;
+        const float sD = diag ? 0.0f : 1.22474487139158905f;
+        const double ex = P.e_out[pr.x] + P.e_out[pr.y];
+        const bool prow = p < P.N;
+        const float uA1 = prow ? P.unitA[(long long)pr.x * P.N + p] : 0.f;
+        const float uA2 = prow ? P.unitA[(long long)pr.y * P.N + p] : 0.f;
+        const float inv_uy = prow ? 1.0f / P.unitY[p] : 0.f;
+        const float inv_uyw = prow ? 1.0f / P.unitYw[p] : 0.f;
+        // this tile's K range of Y: [kS, kS + BN) for S, [kS + BN, kS + 2 BN) for D
+        const long long kS = (long long)pair_local * P.kpp + (long long)(c0 / BN) * KCHUNK;
+        for (int cb = 0; cb < BN; cb += 32) {
+          float h1[32], l1[32], h2[32], l2[32];
+          tc::tmem_ld32(trow + cb, h1);
+          tc::tmem_ld32(trow + BN + cb, l1);
+          if (!diag) {
+            tc::tmem_ld32(trow + 2 * BN + cb, h2);
+            tc::tmem_ld32(trow + 3 * BN + cb, l2);
+          }
+          if (prow) {
+            __nv_bfloat16* y = P.Y + (long long)p * P.Ks + kS;
+            __nv_bfloat16* yw = P.Yw + (long long)p * P.Ks + kS;
+#pragma unroll 2
+            for (int c = 0; c < 32; ++c) {
+              const int cl = cb + c;
+              const int ci = c0 + cl;
+              float ys = 0.f, yd = 0.f, w = 0.f;
+              if (ci < P.n_in) {
+                // B-row units: hole rows (y, c) -> y*v + c ; particle rows (c, y) -> c*v + y
+                const long long rb1 = P.hole ? (long long)pr.y * P.v_stride + ci
+                                             : (long long)ci * P.v_stride + pr.y;
+                const long long rb2 = P.hole ? (long long)pr.x * P.v_stride + ci
+                                             : (long long)ci * P.v_stride + pr.x;
+                const float xa = (h1[c] + l1[c]) * (uA1 * P.unitB[rb1]);
+                const float xb = diag ? xa : (h2[c] + l2[c]) * (uA2 * P.unitB[rb2]);
+                ys = sS * (xa + xb);
+                yd = sD * (xa - xb);
+                w = (float)(ex - P.e_in[ci]);
+              }
+              __nv_bfloat16 a0, a1, a2;
+              tc::slice3f(ys * inv_uy, a0, a1, a2);
+              y[cl] = a0; y[P.plane + cl] = a1; y[2 * P.plane + cl] = a2;
+              tc::slice3f(yd * inv_uy, a0, a1, a2);
+              y[BN + cl] = a0; y[P.plane + BN + cl] = a1; y[2 * P.plane + BN + cl] = a2;
+              tc::slice3f(ys * w * inv_uyw, a0, a1, a2);
+              yw[cl] = a0; yw[P.plane + cl] = a1; yw[2 * P.plane + cl] = a2;
+              tc::slice3f(yd * w * inv_uyw, a0, a1, a2);
+              yw[BN + cl] = a0; yw[P.plane + BN + cl] = a1; yw[2 * P.plane + BN + cl] = a2;
+            }
+          }
+        }
+      } else {
+        const int p = p0 + r;
+        double* U = moment == 0 ? P.U0 : P.U1;
+        const double uA = (p < P.N) ? (double)(moment == 0 ? P.unitA : P.unitA2)[p] : 0.0;
+        for (int cb = 0; cb < BN; cb += 32) {
+          float hi[32], lo[32];
+          tc::tmem_ld32(trow + cb, hi);
+          tc::tmem_ld32(trow + BN + cb, lo);
+          if (p < P.N) {
+#pragma unroll 4
+            for (int c = 0; c < 32; ++c) {
+              const int q = q0 + cb + c;
+              if (q < P.N)
+                atomicAdd(U + (long long)p * P.N + q,
+                          (double)(hi[c] + lo[c]) * (uA * (double)P.unitB[q]));
+            }
+          }
+        }
+      }
+    }
+  }
+
+  tc::tc_fence_before();
+  __syncthreads();
+  if (threadIdx.x == 0 && abort_sh) {
+    atomicExch(P.err, DEV_TIMEOUT);
+    // let copies still in flight land before the shared memory goes away
+    for (int t = consumed_sh; t < issued_sh; ++t) {
+      const long long t0 = clock64();
+      while (!tc::mbar_try_wait(&full_bar[t % STAGES], (t / STAGES) & 1) &&
+             clock64() - t0 < tc::kWaitCycles) {
+      }
+    }
+  }
+  if (warp == 1) {
+    if (abort_sh) {  // MMAs may still be running: wait for the last commit
+      const long long t0 = clock64();
+      while (!tc::mbar_try_wait(&acc_bar, 0) && clock64() - t0 < tc::kWaitCycles) {
+      }
+    }
+    tc::tc_fence_after();
+    tc::tmem_dealloc(tmem, TMEM_COLS);
+  }
+}
+
+// FP64 rows [nrow][ncol] (row stride ld) -> three BF16 limb planes
+// [3][nrow][ncolp] (zero padded to ncolp) in fixed point with the row's
+// power-of-two unit; also the unit and the Euclidean norm of each row.
+// One warp per row.
+__global__ void slice_rows_kernel(const double* __restrict__ src, long long nrow, int ncol,
+                                  long long ld, int ncolp, __nv_bfloat16* __restrict__ dst,
+                                  float* __restrict__ unit, double* __restrict__ norm) {
+  const long long plane = nrow * ncolp;
+  const int lane = threadIdx.x & 31;
+  const long long nwarps = (long long)gridDim.x * (blockDim.x >> 5);
+  for (long long r = (blockIdx.x * (long long)blockDim.x + threadIdx.x) >> 5; r < nrow;
+       r += nwarps) {
+    const double* row = src + r * ld;
+    double m = 0.0, ss = 0.0;
+    for (int c = lane; c < ncol; c += 32) {
+      const double x = row[c];
+      m = fmax(m, fabs(x));
+      ss = fma(x, x, ss);
+    }
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+      m = fmax(m, __shfl_xor_sync(0xffffffffu, m, o));
+      ss += __shfl_xor_sync(0xffffffffu, ss, o);
+    }
+    const double u = tc::slice_unit(m);
+    const double inv = 1.0 / u;  // exact: u is a power of two
+    __nv_bfloat16* d = dst + r * ncolp;
+    for (int c = lane; c < ncolp; c += 32) {
+      const double x = (c < ncol) ? row[c] : 0.0;
+      __nv_bfloat16 h0, h1, h2;
+      tc::slice3(x * inv, h0, h1, h2);
+      d[c] = h0;
+      d[plane + c] = h1;
+      d[2 * plane + c] = h2;
+    }
+    if (lane == 0) {
+      unit[r] = (float)u;
+      norm[r] = sqrt(ss);
+    }
+  }
+}
+
+// Units of the Y and Yw rows of one sector from a Cauchy-Schwarz bound:
+// |X_xy[p,c]| <= |Lx[x][p]| |Lpair[y][c]|, |Y| <= sqrt(6) max|X| (the D part,
+// sqrt(3/2) |X_xy - X_yx|), |Yw| <= |Y| max|w|.  One thread per p.
+__global__ void y_units_kernel(const double* __restrict__ norm_x, int n_out, int N, double bmax,
+                               double wmax, float* __restrict__ unit_y,
+                               float* __restrict__ unit_yw) {
+  const int p = blockIdx.x * blockDim.x + threadIdx.x;
+  if (p >= N) return;
+  double a = 0.0;
+  for (int x = 0; x < n_out; ++x) a = fmax(a, norm_x[(long long)x * N + p]);
+  const double yb = 2.475 * a * bmax;  // sqrt(6) with a 1% margin for rounding
+  unit_y[p] = (float)tc::slice_unit(yb);
+  unit_yw[p] = (float)tc::slice_unit(yb * wmax);
+}
+
+__global__ void max_kernel(const double* __restrict__ x, long long n, double* out) {
+  __shared__ double sh[32];
+  double m = 0.0;
+  for (long long t = threadIdx.x; t < n; t += blockDim.x) m = fmax(m, x[t]);
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) m = fmax(m, __shfl_xor_sync(0xffffffffu, m, o));
+  if ((threadIdx.x & 31) == 0) sh[threadIdx.x >> 5] = m;
+  __syncthreads();
+  if (threadIdx.x < 32) {
+    m = (threadIdx.x < (blockDim.x >> 5)) ? sh[threadIdx.x] : 0.0;
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) m = fmax(m, __shfl_xor_sync(0xffffffffu, m, o));
+    if (threadIdx.x == 0) *out = m;
+  }
+}
+
+// ---------------------------------------------------------------------------
+// host side
+// ---------------------------------------------------------------------------
+PFN_cuTensorMapEncodeTiled_v12000 get_encode() {
+  static PFN_cuTensorMapEncodeTiled_v12000 fn = nullptr;
+  if (!fn) {
+    cudaDriverEntryPointQueryResult q;
+    void* p = nullptr;
+    if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &p, 12000, cudaEnableDefault,
+                                         &q) == cudaSuccess &&
+        q == cudaDriverEntryPointSuccess)
+      fn = reinterpret_cast<PFN_cuTensorMapEncodeTiled_v12000>(p);
+  }
+  return fn;
+}
+
+bool make_map(CUtensorMap* m, const void* base, int rank, const cuuint64_t* dims,
+              const cuuint64_t* strides_bytes, const cuuint32_t* box, std::string& err) {
+  auto enc = get_encode();
+  if (!enc) {
+    err = "cuTensorMapEncodeTiled unavailable";
+    return false;
+  }
+  cuuint32_t es[5] = {1, 1, 1, 1, 1};
+  CUresult r = enc(m, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, rank, const_cast<void*>(base), dims,
+                   strides_bytes, box, es, CU_TENSOR_MAP_INTERLEAVE_NONE,
+                   CU_TENSOR_MAP_SWIZZLE_128B, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
+                   CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+  if (r != CUDA_SUCCESS) {
+    err = "cuTensorMapEncodeTiled failed (" + std::to_string((int)r) + ")";
+    return false;
+  }
+  return true;
+}
+
+struct Buffers {
+  void* p = nullptr;
+  size_t bytes = 0;
+};
+
+struct MixedWs {
+  Buffers lx_o, lx_v, l_ov, y, yw, pairs, err;
+  Buffers u_xo, u_xv, u_ov, n_xo, n_xv, n_ov, u_y, u_yw, scal;
+};
+
+MixedWs g_ws[64];  // per device
+
+template <class T>
+T* grow(Buffers& b, size_t count, std::string& err) {
+  const size_t bytes = std::max<size_t>(count * sizeof(T), 256);
+  if (b.bytes < bytes) {
+    if (b.p) cudaFree(b.p);
+    b.p = nullptr;
+    b.bytes = 0;
+    if (cudaMalloc(&b.p, bytes) != cudaSuccess) {
+      cudaGetLastError();
+      err = "mixed workspace allocation of " + std::to_string(bytes) + " bytes failed";
+      return nullptr;
+    }
+    b.bytes = bytes;
+  }
+  return static_cast<T*>(b.p);
+}
+
+
+}  // namespace
+
+int mixed_build_moments_rotated(const double* Lxo, const double* Lxv, const double* Lov, int naux,
+                                int N, int o, int v, const double* eo, const double* ev,
+                                double* U_hole, double* U_part, std::string& err,
+                                cudaStream_t s) {
+  int dev = 0;
+  cudaGetDevice(&dev);
+  MixedWs& W = g_ws[dev & 63];
+  static bool attr_done[64] = {false};
+  if (!attr_done[dev & 63]) {
+    if (cudaFuncSetAttribute(gemm6_kernel<MODE_PAIR>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                             SMEM_BYTES) != cudaSuccess ||
+        cudaFuncSetAttribute(gemm6_kernel<MODE_MOMENT>,
+                             cudaFuncAttributeMaxDynamicSharedMemorySize, SMEM_BYTES) != cudaSuccess) {
+      err = "cudaFuncSetAttribute(smem) failed";
+      return AGF2_ERR_CUDA;
+    }
+    attr_done[dev & 63] = true;
+  }
+  const int Qs = (naux + BK - 1) / BK * BK;
+  const long long NQs = (long long)N * Qs;
+  __nv_bfloat16* lxo = grow<__nv_bfloat16>(W.lx_o, 3LL * o * NQs, err);
+  __nv_bfloat16* lxv = grow<__nv_bfloat16>(W.lx_v, 3LL * v * NQs, err);
+  __nv_bfloat16* lov = grow<__nv_bfloat16>(W.l_ov, 3LL * o * v * Qs, err);
+  int* derr = grow<int>(W.err, 1, err);
+  if (!lxo || !lxv || !lov || !derr) return AGF2_ERR_OOM;
+  cudaMemsetAsync(derr, 0, sizeof(int), s);
+  float* u_xo = grow<float>(W.u_xo, (size_t)o * N, err);
+  float* u_xv = grow<float>(W.u_xv, (size_t)v * N, err);
+  float* u_ov = grow<float>(W.u_ov, (size_t)o * v, err);
+  double* n_xo = grow<double>(W.n_xo, (size_t)o * N, err);
+  double* n_xv = grow<double>(W.n_xv, (size_t)v * N, err);
+  double* n_ov = grow<double>(W.n_ov, (size_t)o * v, err);
+  float* u_y = grow<float>(W.u_y, N, err);
+  float* u_yw = grow<float>(W.u_yw, N, err);
+  double* scal = grow<double>(W.scal, 8, err);
+  if (!u_xo || !u_xv || !u_ov || !n_xo || !n_xv || !n_ov || !u_y || !u_yw || !scal)
+    return AGF2_ERR_OOM;
+  // rotated FP64 tensors have layout [x][p][Q] / [j][a][Q] with row length naux
+  auto slice = [&](const double* src, long long rows, __nv_bfloat16* dst, float* unit,
+                   double* norm) {
+    const long long blocks = std::min<long long>((rows + 7) / 8, 152LL * 16);
+    slice_rows_kernel<<<(int)std::max(1LL, blocks), 256, 0, s>>>(src, rows, naux, naux, Qs, dst,
+                                                                 unit, norm);
+  };
+  slice(Lxo, (long long)o * N, lxo, u_xo, n_xo);
+  slice(Lxv, (long long)v * N, lxv, u_xv, n_xv);
+  slice(Lov, (long long)o * v, lov, u_ov, n_ov);
+  max_kernel<<<1, 1024, 0, s>>>(n_ov, (long long)o * v, scal);
+  if (cudaGetLastError() != cudaSuccess) {
+    err = "slice kernel launch failed";
+    return AGF2_ERR_CUDA;
+  }
+  double bmax = 0.0;
+  std::vector<double> eoh(o), evh(v);
+  cudaMemcpyAsync(&bmax, scal, sizeof(double), cudaMemcpyDeviceToHost, s);
+  cudaMemcpyAsync(eoh.data(), eo, o * sizeof(double), cudaMemcpyDeviceToHost, s);
+  cudaMemcpyAsync(evh.data(), ev, v * sizeof(double), cudaMemcpyDeviceToHost, s);
+  if (cudaStreamSynchronize(s) != cudaSuccess) {
+    err = "mixed moment build: slicing failed";
+    return AGF2_ERR_CUDA;
+  }
+  const double eo_min = *std::min_element(eoh.begin(), eoh.end());
+  const double eo_max = *std::max_element(eoh.begin(), eoh.end());
+  const double ev_min = *std::min_element(evh.begin(), evh.end());
+  const double ev_max = *std::max_element(evh.begin(), evh.end());
+  // tensor maps of the rotated limb planes
+  CUtensorMap map_xo, map_xv, map_b_hole, map_b_part;
+  {
+    cuuint64_t dims[3] = {(cuuint64_t)Qs, (cuuint64_t)N, (cuuint64_t)3 * o};
+    cuuint64_t str[2] = {(cuuint64_t)Qs * 2, (cuuint64_t)NQs * 2};
+    cuuint32_t box[3] = {BK, BM, 1};
+    if (!make_map(&map_xo, lxo, 3, dims, str, box, err)) return AGF2_ERR_CUDA;
+    dims[2] = (cuuint64_t)3 * v;
+    if (!make_map(&map_xv, lxv, 3, dims, str, box, err)) return AGF2_ERR_CUDA;
+  }
+  {
+    // Lov limbs [3][o][v][Qs]: dims (Q, a, i, limb)
+    cuuint64_t dims[4] = {(cuuint64_t)Qs, (cuuint64_t)v, (cuuint64_t)o, 3};
+    cuuint64_t str[3] = {(cuuint64_t)Qs * 2, (cuuint64_t)v * Qs * 2, (cuuint64_t)o * v * Qs * 2};
+    cuuint32_t box_h[4] = {BK, BN, 1, 1};   // hole: rows a, fixed j
+    cuuint32_t box_p[4] = {BK, 1, BN, 1};   // particle: rows i, fixed b
+    if (!make_map(&map_b_hole, lov, 4, dims, str, box_h, err)) return AGF2_ERR_CUDA;
+    if (!make_map(&map_b_part, lov, 4, dims, str, box_p, err)) return AGF2_ERR_CUDA;
+  }
+
+  const int n_ptiles = (N + BM - 1) / BM;
+  for (int sector = 0; sector < 2; ++sector) {
+    const bool hole = (sector == 0);
+    const int n_out = hole ? o : v;
+    const int n_in = hole ? v : o;
+    const double* e_out = hole ? eo : ev;
+    const double* e_in = hole ? ev : eo;
+    double* U = hole ? U_hole : U_part;
+    // |w| = |e_x + e_y - e_c| is extremal at the ends of the energy ranges
+    const double wmax = hole ? std::max(std::fabs(2 * eo_max - ev_min), std::fabs(2 * eo_min - ev_max))
+                             : std::max(std::fabs(2 * ev_max - eo_min), std::fabs(2 * ev_min - eo_max));
+    y_units_kernel<<<(N + 127) / 128, 128, 0, s>>>(hole ? n_xo : n_xv, n_out, N, bmax, wmax, u_y,
+                                                   u_yw);
+    // unordered pairs x <= y
+    std::vector<int2> pairs;
+    pairs.reserve((size_t)n_out * (n_out + 1) / 2);
+    for (int x = 0; x < n_out; ++x)
+      for (int y = x; y < n_out; ++y) pairs.push_back(make_int2(x, y));
+    int2* dpairs = grow<int2>(W.pairs, pairs.size(), err);
+    if (!dpairs) return AGF2_ERR_OOM;
+    cudaMemcpyAsync(dpairs, pairs.data(), pairs.size() * sizeof(int2), cudaMemcpyHostToDevice, s);
+    const int n_cchunks = (n_in + BN - 1) / BN;
+    const long long kpp = (long long)n_cchunks * KCHUNK;
+    // pairs per block: Y + Yw limb planes of the block stay near L2 size
+    const double per_pair = (double)N * kpp * 2 /*Y,Yw*/ * 3 /*limbs*/ * 2 /*bytes*/;
+    int bp = (int)std::max(1.0, std::floor(96.0e6 / per_pair));
+    bp = std::min<int>(bp, (int)pairs.size());
+    const long long Ks = (long long)bp * kpp;
+    __nv_bfloat16* y = grow<__nv_bfloat16>(W.y, 3LL * N * Ks, err);
+    __nv_bfloat16* yw = grow<__nv_bfloat16>(W.yw, 3LL * N * Ks, err);
+    if (!y || !yw) return AGF2_ERR_OOM;
+    for (size_t b0 = 0; b0 < pairs.size(); b0 += bp) {
+      const int np = (int)std::min<size_t>(bp, pairs.size() - b0);
+      const long long K = (long long)np * kpp;
+      Params P{};
+      P.N = N;
+      P.n_in = n_in;
+      P.ksteps = Qs / BK;
+      P.n_ptiles = n_ptiles;
+      P.n_cchunks = n_cchunks;
+      P.n_out = n_out;
+      P.hole = hole ? 1 : 0;
+      P.pair0 = (int)b0;
+      P.kpp = kpp;
+      P.pairs = dpairs;
+      P.e_out = e_out;
+      P.e_in = e_in;
+      P.unitA = hole ? u_xo : u_xv;
+      P.unitB = u_ov;
+      P.unitY = u_y;
+      P.unitYw = u_yw;
+      P.v_stride = v;
+      P.Y = y;
+      P.Yw = yw;
+      P.Ks = Ks;
+      P.plane = (long long)N * Ks;
+      P.err = derr;
+      const int grid1 = np * n_ptiles * n_cchunks;
+      gemm6_kernel<MODE_PAIR><<<grid1, NTHREADS, SMEM_BYTES, s>>>(
+          hole ? map_xo : map_xv, hole ? map_xo : map_xv, hole ? map_b_hole : map_b_part, P);
+      // GEMM 2 over this block's K = np * kpp
+      CUtensorMap map_y, map_yw;
+      cuuint64_t dims[3] = {(cuuint64_t)K, (cuuint64_t)N, 3};
+      cuuint64_t str[2] = {(cuuint64_t)Ks * 2, (cuuint64_t)N * Ks * 2};
+      cuuint32_t box[3] = {BK, BM, 1};
+      if (!make_map(&map_y, y, 3, dims, str, box, err)) return AGF2_ERR_CUDA;
+      if (!make_map(&map_yw, yw, 3, dims, str, box, err)) return AGF2_ERR_CUDA;
+      Params M{};
+      M.N = N;
+      M.n_ptiles = n_ptiles;
+      M.n_qtiles = (N + BN - 1) / BN;
+      M.ksteps = (int)((K + BK - 1) / BK);
+      const int tiles = M.n_ptiles * M.n_qtiles * 2;
+      int nsplit = std::max(1, (148 * 2 + tiles - 1) / tiles);
+      nsplit = std::min(nsplit, M.ksteps);
+      M.ksplit = (M.ksteps + nsplit - 1) / nsplit;
+      M.nsplit = (M.ksteps + M.ksplit - 1) / M.ksplit;  // every split non-empty
+      M.n_out = 0;
+      M.unitA = u_y;
+      M.unitA2 = u_yw;
+      M.unitB = u_y;
+      M.U0 = U;
+      M.U1 = U + (long long)N * N;
+      M.err = derr;
+      gemm6_kernel<MODE_MOMENT><<<tiles * M.nsplit, NTHREADS, SMEM_BYTES, s>>>(map_y, map_yw,
+                                                                              map_y, M);
+      cudaError_t e = cudaGetLastError();
+      if (e != cudaSuccess) {
+        err = std::string("tcgen05 kernel launch: ") + cudaGetErrorString(e);
+        return AGF2_ERR_CUDA;
+      }
+    }
+  }
+  int herr = 0;
+  cudaMemcpyAsync(&herr, derr, sizeof(int), cudaMemcpyDeviceToHost, s);
+  cudaError_t e = cudaStreamSynchronize(s);
+  if (e != cudaSuccess) {
+    err = std::string("mixed moment build: ") + cudaGetErrorString(e);
+    return AGF2_ERR_CUDA;
+  }
+  if (herr == DEV_TIMEOUT) {
+    err = "tcgen05 pipeline wait timed out";
+    return AGF2_ERR_TIMEOUT;
+  }
+  return AGF2_OK;
+}
+
 }  // namespace agf2
