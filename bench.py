@@ -1,0 +1,364 @@
+#!/usr/bin/env python
+"""AGF2 iteration throughput on one synthetic system (default: nmo=200,
+nocc=40, naux=800, seed 1 -- the synthetic stand-in for a guanine-sized
+molecule).
+
+One step = one full AGF2 iteration at steady state (pole counts of
+iteration >= 2): moment build (split-BF16 tcgen05 path by default),
+compression of both sectors, Fock loop, energies.  W warm-up iterations run
+first (the first from the Hartree-Fock reference), then K timed iterations
+continue the same self-consistency.
+
+Prints one JSON line.  ``--impl reference`` times the FP64 CPU oracle on a
+bounded sample of the same workload instead (no GPU).
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import tempfile
+import time
+from pathlib import Path
+
+ROOT = Path(__file__).resolve().parent
+sys.path.insert(0, str(ROOT))
+
+METRIC = "AGF2 iterations/sec and moment-build TFLOP/s, mixed vs FP64 at ≤1e-5 Ha IP err"
+UNIT = "iterations/s"
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=5)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--config", default="c2")
+    ap.add_argument("--precision", default="bf16x3", choices=["bf16x3", "fp64"])
+    ap.add_argument("--fp64-steps", type=int, default=1,
+                    help="FP64-path iterations timed after the main steps (0: skip)")
+    ap.add_argument("--cpu-seconds", type=float, default=15.0,
+                    help="target CPU time of the oracle sample")
+    ap.add_argument("--no-e2e", action="store_true")
+    return ap.parse_args()
+
+
+def workload_desc(cfg):
+    from paper_2106_03508_gb300.synth import CONFIGS
+    c = CONFIGS[cfg]
+    return {"workload": f"{cfg}: synthetic closed-shell DF system nmo={c['nmo']} nocc={c['nocc']} "
+                        f"naux={c['naux']} seed={c['seed']}, steady-state AGF2(1,0) iterations",
+            "nmo": c["nmo"], "nocc": c["nocc"], "naux": c["naux"], "seed": c["seed"]}
+
+
+# ---------------------------------------------------------------------------
+# CPU oracle sample (cpu_baseline and --impl reference)
+# ---------------------------------------------------------------------------
+def _oracle_setup(cfg):
+    from paper_2106_03508_gb300.synth import CONFIGS, make_config
+    c = CONFIGS[cfg]
+    s = make_config(cfg)
+    N = s.nmo
+    return s, c["nocc"] + N, 3 * N - (c["nocc"] + N)
+
+
+def oracle_time(cfg, k):
+    """Seconds per full iteration extrapolated from one timed FP64-oracle
+    moment build (the O(N^5) step) on a steady-state-shaped pole set with k
+    occupied poles and all v' = 3N - (nocc + N) virtual poles; the rate is
+    scaled by the algorithmic flop ratio to o' = nocc + N.  Fock loop and
+    compression excluded (O(N^3); they would only lower the CPU rate)."""
+    from oracle import agf2_oracle as O
+    from paper_2106_03508_gb300.synth import random_poles
+    s, o_full, v_full = _oracle_setup(cfg)
+    e, C, mu = random_poles(s.nmo, k + v_full, k, 11)
+    t0 = time.perf_counter()
+    O.build_moments(s.L, e, C, mu)
+    dt = time.perf_counter() - t0
+    rate = O.flops_moments(s.nmo, k, v_full, s.naux) / dt
+    return O.flops_moments(s.nmo, o_full, v_full, s.naux) / rate, dt
+
+
+def oracle_calibrate(cfg, target_s):
+    """Smallest sample size k (doubling) whose oracle build takes >= target_s / 2."""
+    s, o_full, v_full = _oracle_setup(cfg)
+    k = 1
+    while True:
+        t_iter, dt = oracle_time(cfg, k)
+        if dt >= target_s / 2 or 2 * k > o_full:
+            return k, t_iter, dt
+        k *= 2
+
+
+def oracle_sample_desc(cfg, k, dt):
+    s, o_full, v_full = _oracle_setup(cfg)
+    return (f"FP64 oracle build_moments on nmo={s.nmo} naux={s.naux} with {k} occupied + "
+            f"{v_full} virtual poles ({dt:.1f} s), extrapolated by algorithmic flops to "
+            f"o'={o_full}, v'={v_full} (one steady-state iteration); moment build only")
+
+
+def run_reference(args):
+    rank = int(os.environ.get("RANK", "0"))
+    if rank != 0:
+        return
+    cores = os.cpu_count()
+    k, _, _ = oracle_calibrate(args.config, args.cpu_seconds / 4)
+    for _ in range(args.warmup):
+        oracle_time(args.config, k)
+    times, dts = [], []
+    for _ in range(args.steps):
+        t, dt = oracle_time(args.config, k)
+        times.append(t)
+        dts.append(dt)
+    t = statistics.median(times)
+    val = 1.0 / t
+    line = {"impl": "reference", "metric": METRIC, "value": val, "unit": UNIT,
+            "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup,
+            "ms_per_step": t * 1e3, "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "config": workload_desc(args.config),
+            "cpu_baseline": {"value": val, "unit": UNIT, "cores": cores, "kind": "oracle",
+                             "sample": oracle_sample_desc(args.config, k, statistics.median(dts))},
+            "e2e": {"value": val, "unit": UNIT, "h2d_bytes_per_step": 0,
+                    "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+
+
+# ---------------------------------------------------------------------------
+# GPU path
+# ---------------------------------------------------------------------------
+class Clocks:
+    Q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+         "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+         "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, device):
+        self.device = device
+        self.f = tempfile.NamedTemporaryFile("w+", suffix=".csv", delete=False)
+        self.p = None
+
+    def start(self):
+        try:
+            self.p = subprocess.Popen(["nvidia-smi", f"--id={self.device}", f"--query-gpu={self.Q}",
+                                       "--format=csv,noheader,nounits", "-lms", "200"],
+                                      stdout=self.f, stderr=subprocess.DEVNULL)
+        except OSError:
+            self.p = None
+
+    def stop(self):
+        if self.p is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        self.p.terminate()
+        self.p.wait()
+        self.f.flush()
+        rows = [r.split(",") for r in Path(self.f.name).read_text().splitlines() if r.strip()]
+        sm = [float(r[1]) for r in rows if len(r) >= 9 and r[1].strip().replace(".", "").isdigit()]
+        smax = [float(r[2]) for r in rows if len(r) >= 9 and r[2].strip().replace(".", "").isdigit()]
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        reasons = set()
+        for r in rows:
+            if len(r) < 9:
+                continue
+            for n, v in zip(names, r[5:9]):
+                if v.strip().lower() == "active":
+                    reasons.add(n)
+        return {"sm_mhz": statistics.median(sm) if sm else None,
+                "sm_max_mhz": max(smax) if smax else None, "reasons": sorted(reasons),
+                "samples": len(sm)}
+
+
+def peaks():
+    p = ROOT / "MEASURED_PEAKS.json"
+    if p.exists():
+        d = json.loads(p.read_text())
+        return d, "measured"
+    return {"hbm_gbs": 6800.0, "bf16_tflops": 1900.0, "bf16_tflops_sustained": 1700.0}, "fallback"
+
+
+def run_ours(args):
+    import torch
+    import torch.distributed as dist
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    if world > 1:
+        torch.cuda.set_device(local)
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+    else:
+        torch.cuda.set_device(0)
+    dev = torch.cuda.current_device()
+
+    from paper_2106_03508_gb300 import build as b
+    b.build()
+    from paper_2106_03508_gb300 import agf2
+    from paper_2106_03508_gb300.synth import make_config
+
+    s = make_config(args.config)
+    N, naux, nelec = s.nmo, s.naux, s.nelec
+    prec = agf2.AGF2_BF16X3 if args.precision == "bf16x3" else agf2.AGF2_FP64
+    h = agf2.Handle(dev)
+    L_host = torch.from_numpy(s.L).pin_memory()
+    eps_host = torch.from_numpy(s.eps).pin_memory()
+    L = L_host.to("cuda", non_blocking=True)
+    eps = eps_host.to("cuda", non_blocking=True)
+    hc = torch.empty(N, N, dtype=torch.float64, device="cuda")
+    agf2.agf2_hcore_from_mo_energies(h.h, L.data_ptr(), naux, N, eps.data_ptr(), s.nocc,
+                                     hc.data_ptr())
+    hc_host = hc.cpu().pin_memory()
+
+    o = agf2.agf2_opts_default()
+    o.precision = prec
+    o.max_iter = max(1, args.warmup)
+    o.resume = 0
+    agf2.agf2_run(h.h, hc.data_ptr(), L.data_ptr(), naux, N, nelec, eps.data_ptr(), o)
+    o.max_iter = 1
+    o.resume = 1
+
+    def barrier():
+        if world > 1:
+            dist.barrier()
+        torch.cuda.synchronize()
+
+    # ---- device-resident timed region ----
+    agf2.agf2_set_profiling(h.h, True)
+    clk = Clocks(dev)
+    results = []
+    barrier()
+    clk.start()
+    n0 = agf2.agf2_launch_count()
+    t_ev0, t_ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    t_ev0.record()
+    for _ in range(args.steps):
+        rc, out = agf2.agf2_run(h.h, hc.data_ptr(), L.data_ptr(), naux, N, nelec, eps.data_ptr(), o)
+        results.append(out.as_dict())
+    t_ev1.record()
+    barrier()
+    launches = agf2.agf2_launch_count() - n0
+    clocks = clk.stop()
+    elapsed = t_ev0.elapsed_time(t_ev1) / 1e3
+    if world > 1:
+        t = torch.tensor([elapsed], device="cuda")
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        elapsed = float(t.item())
+    k_stats = {kind: agf2.agf2_kernel_stats(h.h, kind) for kind in (0, 1)}
+    agf2.agf2_set_profiling(h.h, False)
+    value = world * args.steps / elapsed
+    ms_per_step = elapsed / args.steps * 1e3
+
+    # ---- end to end through the C ABI with host buffers ----
+    e2e = None
+    if not args.no_e2e:
+        e_out = torch.empty(3 * N, dtype=torch.float64).pin_memory()
+        e_dev = torch.empty(3 * N, dtype=torch.float64, device="cuda")
+        L2 = torch.empty_like(L)
+        hc2 = torch.empty_like(hc)
+        eps2 = torch.empty_like(eps)
+        barrier()
+        t0 = time.perf_counter()
+        for _ in range(args.steps):
+            L2.copy_(L_host, non_blocking=True)
+            hc2.copy_(hc_host, non_blocking=True)
+            eps2.copy_(eps_host, non_blocking=True)
+            agf2.agf2_run(h.h, hc2.data_ptr(), L2.data_ptr(), naux, N, nelec, eps2.data_ptr(), o)
+            agf2.agf2_get_state(h.h, e=e_dev.data_ptr())
+            e_out.copy_(e_dev, non_blocking=True)
+        barrier()
+        e_el = time.perf_counter() - t0
+        if world > 1:
+            t = torch.tensor([e_el], device="cuda")
+            dist.all_reduce(t, op=dist.ReduceOp.MAX)
+            e_el = float(t.item())
+        e2e = {"value": world * args.steps / e_el, "unit": UNIT,
+               "h2d_bytes_per_step": int(L_host.numel() * 8 + hc_host.numel() * 8 + eps_host.numel() * 8),
+               "d2h_bytes_per_step": int(e_out.numel() * 8)}
+
+    # ---- FP64 path on the same state (mixed vs FP64 per iteration) ----
+    fp64 = None
+    if args.fp64_steps > 0 and prec != agf2.AGF2_FP64:
+        of = agf2.agf2_opts_default()
+        of.precision = agf2.AGF2_FP64
+        of.max_iter = 1
+        of.resume = 1
+        barrier()
+        t0 = time.perf_counter()
+        fr = []
+        for _ in range(args.fp64_steps):
+            rc, out = agf2.agf2_run(h.h, hc.data_ptr(), L.data_ptr(), naux, N, nelec,
+                                    eps.data_ptr(), of)
+            fr.append(out.as_dict())
+        barrier()
+        dt = (time.perf_counter() - t0) / args.fp64_steps
+        fp64 = {"iterations_per_s": 1.0 / dt, "s_per_iter": dt,
+                "moment_s": statistics.mean(r["t_moments"] for r in fr),
+                "moment_tflops": statistics.mean(r["flops_moments"] / r["t_moments"] / 1e12
+                                                 for r in fr),
+                "mixed_speedup_per_iter": (args.steps / elapsed) * dt}
+
+    if rank != 0:
+        h.close()
+        if world > 1:
+            dist.destroy_process_group()
+        return
+
+    pk, src = peaks()
+    dominant = max((0, 1), key=lambda k: k_stats[k][1])
+    n_l, ms_l, fl_l = k_stats[dominant]
+    achieved = fl_l / (ms_l / 1e3) / 1e12 if ms_l > 0 else 0.0
+    peak = pk.get("bf16_tflops_sustained", pk.get("bf16_tflops"))
+    kname = {0: "gemm6_kernel<PAIR> (GEMM 1 + S/D/weight epilogue)",
+             1: "gemm6_kernel<MOMENT> (GEMM 2 into U)"}
+    mom_t = statistics.mean(r["t_moments"] for r in results)
+    mom_fl = statistics.mean(r["flops_moments"] for r in results)
+    line = {
+        "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": ms_per_step, "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None,
+        "dtype": "bf16x3" if prec == agf2.AGF2_BF16X3 else "f64", "data": "synthetic",
+        "config": {**workload_desc(args.config), "precision": args.precision,
+                   "l2": "inputs larger than L2 (L = %.0f MB FP64)" % (L.numel() * 8 / 1e6),
+                   "parallelism": "replicas" if world > 1 else "single"},
+        "stage_seconds_per_iter": {k: statistics.mean(r[k] for r in results)
+                                   for k in ("t_moments", "t_compress", "t_fock", "t_energy")},
+        "moment_build": {"tflops_algorithmic": mom_fl / mom_t / 1e12, "flops_per_iter": mom_fl,
+                         "seconds": mom_t},
+        "roofline": {"bound": "tensor", "kernel": kname[dominant], "launches": n_l,
+                     "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
+                     "frac": achieved / peak if peak else None, "traffic": None,
+                     "issued_tflops": 6 * achieved,
+                     "peak_source": f"bf16_tflops_sustained ({src})",
+                     "note": "achieved counts algorithmic flops; the three-limb BF16 scheme issues "
+                             "6 limb products per algorithmic product"},
+        "other_kernel": {"kernel": kname[1 - dominant], "launches": k_stats[1 - dominant][0],
+                         "ms": k_stats[1 - dominant][1],
+                         "tflops": (k_stats[1 - dominant][2] / (k_stats[1 - dominant][1] / 1e3) / 1e12
+                                    if k_stats[1 - dominant][1] > 0 else None)},
+        "gpu_launches": launches,
+        "clocks": clocks,
+        "e2e": e2e,
+        "fp64_path": fp64,
+        "last_energies": {k: results[-1][k] for k in ("E_tot", "ip", "ea", "mu")},
+    }
+    if rank == 0 and world == 1:
+        k, t_iter, dt = oracle_calibrate(args.config, args.cpu_seconds)
+        line["cpu_baseline"] = {"value": 1.0 / t_iter, "unit": UNIT, "cores": os.cpu_count(),
+                                "kind": "oracle", "sample": oracle_sample_desc(args.config, k, dt)}
+    print(json.dumps(line), flush=True)
+    h.close()
+    if world > 1:
+        dist.destroy_process_group()
+
+
+def main():
+    args = parse()
+    if args.impl == "reference":
+        run_reference(args)
+    else:
+        run_ours(args)
+
+
+if __name__ == "__main__":
+    main()

@@ -190,6 +190,23 @@ int agf2_run(agf2_handle h, const double* hcore, const double* L, int naux, int 
  */
 int agf2_get_state(agf2_handle h, double* e, double* C, double* D, int* nqmo);
 
+/*
+ * Opt-in timing of the split-precision tensor-core kernels: with enable = 1
+ * every launch of the pair GEMM (kind 0: GEMM 1 of the moment build with its
+ * S/D and energy-weight epilogue) and of the moment GEMM (kind 1: GEMM 2 into
+ * U) is bracketed by CUDA events on the handle's stream; agf2_kernel_stats
+ * returns, since the last agf2_set_profiling call, the number of launches,
+ * their summed duration (ms) and their algorithmic flop count (the ordered
+ * pole pairs' share of N o' v' (o'+v') [2 n_Q + 2 (nmom+1) N]).  Timing
+ * adds event records and is off by default.
+ */
+int agf2_set_profiling(agf2_handle h, int enable);
+int agf2_kernel_stats(agf2_handle h, int kind, long long* launches, double* ms, double* flops);
+
+/* Number of CUDA kernels this library has launched since it was loaded
+   (all handles; counts kernels issued by cuSOLVER/cuBLAS calls as zero). */
+long long agf2_launch_count(void);
+
 #ifdef __cplusplus
 }
 #endif

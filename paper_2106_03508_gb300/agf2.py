@@ -30,7 +30,7 @@ EXPORTED = [
     "agf2_create", "agf2_destroy", "agf2_set_stream", "agf2_last_error",
     "agf2_hcore_from_mo_energies", "agf2_build_moments", "agf2_compress",
     "agf2_fock_opts_default", "agf2_fock_loop", "agf2_opts_default", "agf2_run",
-    "agf2_get_state",
+    "agf2_get_state", "agf2_set_profiling", "agf2_kernel_stats", "agf2_launch_count",
 ]
 
 
@@ -82,6 +82,10 @@ def _load():
         "agf2_opts_default": (V, [ct.POINTER(agf2_opts)]),
         "agf2_run": (I, [P, P, P, I, I, I, P, ct.POINTER(agf2_opts), ct.POINTER(agf2_result)]),
         "agf2_get_state": (I, [P, P, P, P, ct.POINTER(ct.c_int)]),
+        "agf2_set_profiling": (I, [P, I]),
+        "agf2_kernel_stats": (I, [P, I, ct.POINTER(ct.c_longlong), ct.POINTER(D),
+                                  ct.POINTER(D)]),
+        "agf2_launch_count": (ct.c_longlong, []),
     }
     for name, (res, args) in sig.items():
         fn = getattr(lib, name)
@@ -173,6 +177,20 @@ def agf2_get_state(h, e=None, C=None, D=None):
     nq = ct.c_int()
     _check(h, _lib.agf2_get_state(h, e, C, D, ct.byref(nq)))
     return nq.value
+
+
+def agf2_set_profiling(h, enable: bool):
+    return _check(h, _lib.agf2_set_profiling(h, 1 if enable else 0))
+
+
+def agf2_kernel_stats(h, kind: int):
+    n, ms, fl = ct.c_longlong(), ct.c_double(), ct.c_double()
+    _check(h, _lib.agf2_kernel_stats(h, kind, ct.byref(n), ct.byref(ms), ct.byref(fl)))
+    return n.value, ms.value, fl.value
+
+
+def agf2_launch_count() -> int:
+    return int(_lib.agf2_launch_count())
 
 
 # ---- torch-tensor conveniences (marshalling only) ----

@@ -6,6 +6,18 @@
 
 namespace agf2 {
 
+// Number of kernels this library has launched (all devices, all handles).
+void count_launch(long long n = 1);
+
+// Per-kernel-kind timing of the split-precision kernels (opt-in): CUDA events
+// bracket every launch; durations are summed when the stream is synchronised.
+struct KernelStats {
+  bool enabled = false;
+  long long launches[2] = {0, 0};   // 0: pair GEMM (GEMM 1 + epilogue), 1: moment GEMM
+  double ms[2] = {0.0, 0.0};
+  double flops[2] = {0.0, 0.0};     // algorithmic flops of those launches
+};
+
 // Generic strided, two-level-batched FP64 GEMM:
 //   C[z][m][n] = alpha * sum_k A[z][m][k] * B[z][k][n] + beta * C[z][m][n]
 // with element (m,k) of A at A + off_A(z) + m*sAm + k*sAk (likewise B, C) and
@@ -17,6 +29,8 @@ struct DGemm {
   double* C = nullptr;       long long sCm = 0, sCn = 0, sC1 = 0, sC2 = 0;
   int nb1 = 1, nb2 = 1;
   double alpha = 1.0, beta = 0.0;
+  bool atomic = false;  // C += alpha A B with atomicAdd (beta ignored)
+  int ksplit = 1;       // split K over this many CTAs (requires atomic)
 };
 cudaError_t dgemm(const DGemm& g, cudaStream_t s);
 
@@ -76,6 +90,6 @@ cudaError_t add_scalar(double* x, double a, int n, cudaStream_t s);
 int mixed_build_moments_rotated(const double* Lxo, const double* Lxv, const double* Lov, int naux,
                                 int N, int o, int v, const double* eo, const double* ev,
                                 double* U_hole, double* U_part, std::string& err,
-                                cudaStream_t s);
+                                cudaStream_t s, KernelStats* stats);
 
 }  // namespace agf2

@@ -21,6 +21,9 @@
 #include "agf2_internal.h"
 
 using namespace agf2;
+namespace agf2 {
+long long launch_count();
+}
 
 struct agf2_context {
   int device = 0;
@@ -37,6 +40,7 @@ struct agf2_context {
   double mu = 0.0, E_prev = 0.0, E_hf = 0.0;
   bool have_uprev = false;
   int iter = 0;
+  KernelStats stats;
 };
 
 namespace {
@@ -248,12 +252,14 @@ void sector_fp64(agf2_context* ctx, const Sector& S, int N, int naux, double* U0
       CK(sd_epilogue_fp64(XIJ, XJI, N, nI, nJ, S.n_in, S.e_out + I0, S.e_out + J0, S.e_in, diag, Y,
                           Yw, s));
       for (int n = 0; n < 2; ++n) {
-        DGemm g;  // U^(n) += Z Y^T, Z = Y (n = 0) or Yw (n = 1), K = 2 K1
+        DGemm g;  // U^(n) += Z Y^T, Z = Y (n = 0) or Yw (n = 1), K = 2 K1, split over K
         g.M = N; g.N = N; g.K = (int)(2 * K1);
         g.A = n == 0 ? Y : Yw; g.sAm = 2 * K1; g.sAk = 1;
         g.B = Y; g.sBk = 1; g.sBn = 2 * K1;
         g.C = n == 0 ? U0 : U1; g.sCm = N; g.sCn = 1;
-        g.beta = 1.0;
+        g.atomic = true;
+        const int tiles = ((N + 63) / 64) * ((N + 63) / 64);
+        g.ksplit = std::max(1, std::min<int>((int)(2 * K1 / 256), (2 * 152 + tiles - 1) / tiles));
         CK(dgemm(g, s));
       }
     }
@@ -325,7 +331,8 @@ void build_moments_impl(agf2_context* ctx, const double* L, int naux, int N, con
     CK(dgemm(g, s));
   }
   if (precision == AGF2_BF16X3) {
-    int rc = mixed_build_moments_rotated(Lxo, Lxv, Lov, naux, N, o, v, eo, ev, Uh, Up, ctx->err, s);
+    int rc = mixed_build_moments_rotated(Lxo, Lxv, Lov, naux, N, o, v, eo, ev, Uh, Up, ctx->err, s,
+                                         &ctx->stats);
     if (rc != AGF2_OK) throw Fail{rc};
   } else {
     Sector hole{o, v, Lxo, Lov, (long long)v * naux, (long long)naux, eo, ev};
@@ -964,6 +971,24 @@ int agf2_run(agf2_handle h, const double* hcore, const double* L, int naux, int 
   });
   return rc != AGF2_OK ? rc : rc_conv;
 }
+
+int agf2_set_profiling(agf2_handle h, int enable) {
+  return guarded(h, [&](agf2_context* ctx) {
+    ctx->stats = KernelStats();
+    ctx->stats.enabled = enable != 0;
+  });
+}
+
+int agf2_kernel_stats(agf2_handle h, int kind, long long* launches, double* ms, double* flops) {
+  return guarded(h, [&](agf2_context* ctx) {
+    if (kind < 0 || kind > 1) fail(ctx, AGF2_ERR_INVALID_ARG, "kind must be 0 or 1");
+    if (launches) *launches = ctx->stats.launches[kind];
+    if (ms) *ms = ctx->stats.ms[kind];
+    if (flops) *flops = ctx->stats.flops[kind];
+  });
+}
+
+long long agf2_launch_count(void) { return launch_count(); }
 
 int agf2_get_state(agf2_handle h, double* e, double* C, double* D, int* nqmo) {
   return guarded(h, [&](agf2_context* ctx) {

@@ -24,7 +24,12 @@ __global__ void __launch_bounds__(NT) dgemm_kernel(DGemm g) {
   const double* __restrict__ A = g.A + b1 * g.sA1 + b2 * g.sA2;
   const double* __restrict__ B = g.B + b1 * g.sB1 + b2 * g.sB2;
   double* C = g.C + b1 * g.sC1 + b2 * g.sC2;
-  const int m0 = blockIdx.y * BM, n0 = blockIdx.x * BN;
+  const int m0 = blockIdx.y * BM;
+  const int nblk = (g.N + BN - 1) / BN;
+  const int n0 = (blockIdx.x % nblk) * BN;
+  const int ks = blockIdx.x / nblk;  // K split index
+  const int kchunk = ((g.K + g.ksplit - 1) / g.ksplit + BK - 1) / BK * BK;
+  const int kbeg = ks * kchunk, kend = min(g.K, kbeg + kchunk);
   const int tid = threadIdx.x, tx = tid & 15, ty = tid >> 4;
   const bool a_kc = (g.sAk == 1);
   const bool b_nc = (g.sBn == 1);
@@ -34,18 +39,18 @@ __global__ void __launch_bounds__(NT) dgemm_kernel(DGemm g) {
 #pragma unroll
     for (int j = 0; j < 4; ++j) acc[i][j] = 0.0;
 
-  for (int k0 = 0; k0 < g.K; k0 += BK) {
+  for (int k0 = kbeg; k0 < kend; k0 += BK) {
 #pragma unroll
     for (int r = 0; r < 4; ++r) {
       const int e = tid + r * NT;
       int mm, kk;
       if (a_kc) { mm = e / BK; kk = e % BK; } else { mm = e % BM; kk = e / BM; }
       const int gm = m0 + mm, gk = k0 + kk;
-      As[kk][mm] = (gm < g.M && gk < g.K) ? A[gm * g.sAm + gk * g.sAk] : 0.0;
+      As[kk][mm] = (gm < g.M && gk < kend) ? A[gm * g.sAm + gk * g.sAk] : 0.0;
       int nn;
       if (b_nc) { nn = e % BN; kk = e / BN; } else { nn = e / BK; kk = e % BK; }
       const int gn = n0 + nn, gk2 = k0 + kk;
-      Bs[kk][nn] = (gn < g.N && gk2 < g.K) ? B[gk2 * g.sBk + gn * g.sBn] : 0.0;
+      Bs[kk][nn] = (gn < g.N && gk2 < kend) ? B[gk2 * g.sBk + gn * g.sBn] : 0.0;
     }
     __syncthreads();
 #pragma unroll
@@ -72,7 +77,8 @@ __global__ void __launch_bounds__(NT) dgemm_kernel(DGemm g) {
       if (gn >= g.N) continue;
       double* c = C + gm * g.sCm + gn * g.sCn;
       const double v = g.alpha * acc[i][j];
-      *c = (g.beta == 0.0) ? v : fma(g.beta, *c, v);
+      if (g.atomic) atomicAdd(c, v);
+      else *c = (g.beta == 0.0) ? v : fma(g.beta, *c, v);
     }
   }
 }
@@ -333,10 +339,15 @@ __global__ void add_scalar_kernel(double* x, double a, int n) {
 
 }  // namespace
 
+static long long g_launches = 0;
+void count_launch(long long n) { __atomic_fetch_add(&g_launches, n, __ATOMIC_RELAXED); }
+long long launch_count() { return __atomic_load_n(&g_launches, __ATOMIC_RELAXED); }
+
 cudaError_t dgemm(const DGemm& g, cudaStream_t s) {
   if (g.M <= 0 || g.N <= 0 || g.nb1 <= 0 || g.nb2 <= 0) return cudaSuccess;
   const long long nz = (long long)g.nb1 * g.nb2;
-  dim3 grid((g.N + BN - 1) / BN, (g.M + BM - 1) / BM, 1);
+  if (g.ksplit > 1 && !g.atomic) return cudaErrorInvalidValue;
+  dim3 grid(((g.N + BN - 1) / BN) * std::max(1, g.ksplit), (g.M + BM - 1) / BM, 1);
   // gridDim.z is limited to 65535: split large batches over several launches,
   // each covering whole b1 rows.
   const long long lim = (65535LL / g.nb2) * g.nb2;
@@ -351,6 +362,7 @@ cudaError_t dgemm(const DGemm& g, cudaStream_t s) {
     h.nb1 = (int)(chunk / g.nb2);
     grid.z = (unsigned)chunk;
     dgemm_kernel<<<grid, NT, 0, s>>>(h);
+    count_launch();
     z0 += chunk;
   }
   return cudaGetLastError();
@@ -365,6 +377,7 @@ cudaError_t sd_epilogue_fp64(const double* XIJ, const double* XJI, int nmo, int 
   const long long total = (long long)nmo * nI * nJ * n_in;
   sd_epilogue_kernel<<<grid_for(total), 256, 0, s>>>(XIJ, diag ? XIJ : XJI, nmo, nI, nJ, n_in,
                                                       e_outI, e_outJ, e_in, sS, sD, Y, Yw);
+  count_launch();
   return cudaGetLastError();
 }
 
@@ -372,22 +385,26 @@ cudaError_t gather_columns(const double* C, int nrow, int ncol_src, const int* i
                            double* out, cudaStream_t s) {
   if (n <= 0) return cudaSuccess;
   gather_columns_kernel<<<grid_for((long long)nrow * n), 256, 0, s>>>(C, nrow, ncol_src, idx, n, out);
+  count_launch();
   return cudaGetLastError();
 }
 
 cudaError_t gather_vec(const double* e, const int* idx, int n, double* out, cudaStream_t s) {
   if (n <= 0) return cudaSuccess;
   gather_vec_kernel<<<(n + 255) / 256, 256, 0, s>>>(e, idx, n, out);
+  count_launch();
   return cudaGetLastError();
 }
 
 cudaError_t symmetrize(double* U, int n, int nmat, cudaStream_t s) {
   symmetrize_kernel<<<grid_for((long long)nmat * n * n), 256, 0, s>>>(U, n, nmat);
+  count_launch();
   return cudaGetLastError();
 }
 
 cudaError_t axpby(double* y, const double* x, double a, double b, long long n, cudaStream_t s) {
   axpby_kernel<<<grid_for(n), 256, 0, s>>>(y, x, a, b, n);
+  count_launch();
   return cudaGetLastError();
 }
 
@@ -395,30 +412,37 @@ cudaError_t build_extended_h(const double* F, const double* E, const double* v, 
                              int nmo, int nse, double* H, cudaStream_t s) {
   const long long n = nmo + nse;
   build_h_kernel<<<grid_for(n * n), 256, 0, s>>>(F, E, v, delta, nmo, nse, H);
+  count_launch();
   return cudaGetLastError();
 }
 
 cudaError_t column_weights(const double* V, int ld, int nmo, int ncol, double* w, cudaStream_t s) {
   column_weights_kernel<<<(ncol * 32 + 255) / 256, 256, 0, s>>>(V, ld, nmo, ncol, w);
+  count_launch();
   return cudaGetLastError();
 }
 
 cudaError_t physical_block(const double* V, int ld, int nmo, int ncol, double* out, cudaStream_t s) {
   physical_block_kernel<<<grid_for((long long)nmo * ncol), 256, 0, s>>>(V, ld, nmo, ncol, out);
+  count_launch();
   return cudaGetLastError();
 }
 
 cudaError_t dot(const double* a, const double* b, long long n, double* out, double* scratch,
                 cudaStream_t s) {
   dot_partial<<<RED_BLOCKS, RED_THREADS, 0, s>>>(a, b, n, scratch);
+  count_launch();
   final_sum<<<1, RED_THREADS, 0, s>>>(scratch, RED_BLOCKS, out);
+  count_launch();
   return cudaGetLastError();
 }
 
 cudaError_t max_abs_diff(const double* a, const double* b, long long n, double* out, double* scratch,
                          cudaStream_t s) {
   maxdiff_partial<<<RED_BLOCKS, RED_THREADS, 0, s>>>(a, b, n, scratch);
+  count_launch();
   final_max<<<1, RED_THREADS, 0, s>>>(scratch, RED_BLOCKS, out);
+  count_launch();
   return cudaGetLastError();
 }
 
@@ -426,48 +450,58 @@ cudaError_t coulomb_from_gamma(const double* L, const double* gamma, int naux, i
                                cudaStream_t s) {
   const long long nn = (long long)nmo * nmo;
   coulomb_kernel<<<grid_for(nn), 256, 0, s>>>(L, gamma, naux, nn, J);
+  count_launch();
   return cudaGetLastError();
 }
 
 cudaError_t gamma_from_y(const double* Y, const double* Cocc, int nmo, int naux, int k,
                          double* gamma, cudaStream_t s) {
   gamma_kernel<<<naux, RED_THREADS, 0, s>>>(Y, Cocc, nmo, naux, k, gamma);
+  count_launch();
   return cudaGetLastError();
 }
 
 cudaError_t fock_combine(const double* h, const double* J, const double* K, long long n, double* F,
                          cudaStream_t s) {
   fock_combine_kernel<<<grid_for(n), 256, 0, s>>>(h, J, K, n, F);
+  count_launch();
   return cudaGetLastError();
 }
 
 cudaError_t gm_energy(const double* V, const double* e, const double* E, int k, int nse,
                       double* out, double* scratch, cudaStream_t s) {
   gm_partial<<<RED_BLOCKS, RED_THREADS, 0, s>>>(V, e, E, k, nse, scratch);
+  count_launch();
   final_sum<<<1, RED_THREADS, 0, s>>>(scratch, RED_BLOCKS, out);
+  count_launch();
   return cudaGetLastError();
 }
 
 cudaError_t shift_derivative(const double* S, const double* w, int k, int nv, double* out,
                              double* scratch, cudaStream_t s) {
   deriv_partial<<<RED_BLOCKS, RED_THREADS, 0, s>>>(S, w, k, nv, scratch);
+  count_launch();
   final_sum<<<1, RED_THREADS, 0, s>>>(scratch, RED_BLOCKS, out);
+  count_launch();
   return cudaGetLastError();
 }
 
 cudaError_t set_identity(double* A, int n, double scale, cudaStream_t s) {
   set_identity_kernel<<<grid_for((long long)n * n), 256, 0, s>>>(A, n, scale);
+  count_launch();
   return cudaGetLastError();
 }
 
 cudaError_t diag_from_vec(const double* d, int n, double* A, cudaStream_t s) {
   diag_from_vec_kernel<<<grid_for((long long)n * n), 256, 0, s>>>(d, n, A);
+  count_launch();
   return cudaGetLastError();
 }
 
 cudaError_t add_scalar(double* x, double a, int n, cudaStream_t s) {
   if (n <= 0) return cudaSuccess;
   add_scalar_kernel<<<(n + 255) / 256, 256, 0, s>>>(x, a, n);
+  count_launch();
   return cudaGetLastError();
 }
 

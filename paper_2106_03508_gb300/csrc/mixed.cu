@@ -269,34 +269,41 @@ gemm6_kernel(const __grid_constant__ CUtensorMap mapA, const __grid_constant__ C
             tc::tmem_ld32(trow + 3 * BN + cb, l2);
           }
           if (prow) {
-            __nv_bfloat16* y = P.Y + (long long)p * P.Ks + kS;
-            __nv_bfloat16* yw = P.Yw + (long long)p * P.Ks + kS;
-#pragma unroll 2
-            for (int c = 0; c < 32; ++c) {
-              const int cl = cb + c;
-              const int ci = c0 + cl;
-              float ys = 0.f, yd = 0.f, w = 0.f;
-              if (ci < P.n_in) {
-                // B-row units: hole rows (y, c) -> y*v + c ; particle rows (c, y) -> c*v + y
-                const long long rb1 = P.hole ? (long long)pr.y * P.v_stride + ci
-                                             : (long long)ci * P.v_stride + pr.y;
-                const long long rb2 = P.hole ? (long long)pr.x * P.v_stride + ci
-                                             : (long long)ci * P.v_stride + pr.x;
-                const float xa = (h1[c] + l1[c]) * (uA1 * P.unitB[rb1]);
-                const float xb = diag ? xa : (h2[c] + l2[c]) * (uA2 * P.unitB[rb2]);
-                ys = sS * (xa + xb);
-                yd = sD * (xa - xb);
-                w = (float)(ex - P.e_in[ci]);
+            __nv_bfloat16* y = P.Y + (long long)p * P.Ks + kS + cb;
+            __nv_bfloat16* yw = P.Yw + (long long)p * P.Ks + kS + cb;
+            // 8 columns at a time -> one 16-byte store per (array, limb)
+            for (int g = 0; g < 32; g += 8) {
+              uint4 out[12];
+              __nv_bfloat16* ob = reinterpret_cast<__nv_bfloat16*>(out);
+#pragma unroll
+              for (int c = 0; c < 8; ++c) {
+                const int ci = c0 + cb + g + c;
+                float ys = 0.f, yd = 0.f, w = 0.f;
+                if (ci < P.n_in) {
+                  // B-row units: hole rows (y, c) -> y*v + c ; particle rows (c, y) -> c*v + y
+                  const long long rb1 = P.hole ? (long long)pr.y * P.v_stride + ci
+                                               : (long long)ci * P.v_stride + pr.y;
+                  const long long rb2 = P.hole ? (long long)pr.x * P.v_stride + ci
+                                               : (long long)ci * P.v_stride + pr.x;
+                  const float xa = (h1[g + c] + l1[g + c]) * (uA1 * P.unitB[rb1]);
+                  const float xb = diag ? xa : (h2[g + c] + l2[g + c]) * (uA2 * P.unitB[rb2]);
+                  ys = sS * (xa + xb);
+                  yd = sD * (xa - xb);
+                  w = (float)(ex - P.e_in[ci]);
+                }
+                // out[3*arr + limb], arr: 0 Y_S, 1 Y_D, 2 Yw_S, 3 Yw_D
+                tc::slice3f(ys * inv_uy, ob[0 * 8 + c], ob[1 * 8 + c], ob[2 * 8 + c]);
+                tc::slice3f(yd * inv_uy, ob[3 * 8 + c], ob[4 * 8 + c], ob[5 * 8 + c]);
+                tc::slice3f(ys * w * inv_uyw, ob[6 * 8 + c], ob[7 * 8 + c], ob[8 * 8 + c]);
+                tc::slice3f(yd * w * inv_uyw, ob[9 * 8 + c], ob[10 * 8 + c], ob[11 * 8 + c]);
               }
-              __nv_bfloat16 a0, a1, a2;
-              tc::slice3f(ys * inv_uy, a0, a1, a2);
-              y[cl] = a0; y[P.plane + cl] = a1; y[2 * P.plane + cl] = a2;
-              tc::slice3f(yd * inv_uy, a0, a1, a2);
-              y[BN + cl] = a0; y[P.plane + BN + cl] = a1; y[2 * P.plane + BN + cl] = a2;
-              tc::slice3f(ys * w * inv_uyw, a0, a1, a2);
-              yw[cl] = a0; yw[P.plane + cl] = a1; yw[2 * P.plane + cl] = a2;
-              tc::slice3f(yd * w * inv_uyw, a0, a1, a2);
-              yw[BN + cl] = a0; yw[P.plane + BN + cl] = a1; yw[2 * P.plane + BN + cl] = a2;
+#pragma unroll
+              for (int l = 0; l < 3; ++l) {
+                *reinterpret_cast<uint4*>(y + l * P.plane + g) = out[0 + l];
+                *reinterpret_cast<uint4*>(y + l * P.plane + BN + g) = out[3 + l];
+                *reinterpret_cast<uint4*>(yw + l * P.plane + g) = out[6 + l];
+                *reinterpret_cast<uint4*>(yw + l * P.plane + BN + g) = out[9 + l];
+              }
             }
           }
         }
@@ -488,7 +495,26 @@ T* grow(Buffers& b, size_t count, std::string& err) {
 int mixed_build_moments_rotated(const double* Lxo, const double* Lxv, const double* Lov, int naux,
                                 int N, int o, int v, const double* eo, const double* ev,
                                 double* U_hole, double* U_part, std::string& err,
-                                cudaStream_t s) {
+                                cudaStream_t s, KernelStats* stats) {
+  // CUDA events around the tcgen05 launches when stats->enabled
+  std::vector<cudaEvent_t> evs;
+  std::vector<int> ev_kind;
+  std::vector<double> ev_flops;
+  auto mark = [&](int kind, double flops) {
+    if (!stats || !stats->enabled) return;
+    cudaEvent_t a, b;
+    cudaEventCreate(&a);
+    cudaEventCreate(&b);
+    evs.push_back(a);
+    evs.push_back(b);
+    ev_kind.push_back(kind);
+    ev_flops.push_back(flops);
+    cudaEventRecord(a, s);
+  };
+  auto mark_end = [&]() {
+    if (!stats || !stats->enabled) return;
+    cudaEventRecord(evs.back(), s);
+  };
   int dev = 0;
   cudaGetDevice(&dev);
   MixedWs& W = g_ws[dev & 63];
@@ -529,6 +555,7 @@ int mixed_build_moments_rotated(const double* Lxo, const double* Lxv, const doub
     slice_rows_kernel<<<(int)std::max(1LL, blocks), 256, 0, s>>>(src, rows, naux, naux, Qs, dst,
                                                                  unit, norm);
   };
+  count_launch(4);  // three slicing kernels and the max reduction
   slice(Lxo, (long long)o * N, lxo, u_xo, n_xo);
   slice(Lxv, (long long)v * N, lxv, u_xv, n_xv);
   slice(Lov, (long long)o * v, lov, u_ov, n_ov);
@@ -583,6 +610,7 @@ int mixed_build_moments_rotated(const double* Lxo, const double* Lxv, const doub
                              : std::max(std::fabs(2 * ev_max - eo_min), std::fabs(2 * ev_min - eo_max));
     y_units_kernel<<<(N + 127) / 128, 128, 0, s>>>(hole ? n_xo : n_xv, n_out, N, bmax, wmax, u_y,
                                                    u_yw);
+    count_launch();
     // unordered pairs x <= y
     std::vector<int2> pairs;
     pairs.reserve((size_t)n_out * (n_out + 1) / 2);
@@ -628,8 +656,14 @@ int mixed_build_moments_rotated(const double* Lxo, const double* Lxv, const doub
       P.plane = (long long)N * Ks;
       P.err = derr;
       const int grid1 = np * n_ptiles * n_cchunks;
+      // algorithmic flops: GEMM 1 for the ordered pairs of this block
+      long long ordered = 0;
+      for (int t = 0; t < np; ++t) ordered += (pairs[b0 + t].x == pairs[b0 + t].y) ? 1 : 2;
+      mark(0, 2.0 * N * (double)naux * n_in * (double)ordered);
       gemm6_kernel<MODE_PAIR><<<grid1, NTHREADS, SMEM_BYTES, s>>>(
           hole ? map_xo : map_xv, hole ? map_xo : map_xv, hole ? map_b_hole : map_b_part, P);
+      mark_end();
+      count_launch();
       // GEMM 2 over this block's K = np * kpp
       CUtensorMap map_y, map_yw;
       cuuint64_t dims[3] = {(cuuint64_t)K, (cuuint64_t)N, 3};
@@ -654,8 +688,12 @@ int mixed_build_moments_rotated(const double* Lxo, const double* Lxv, const doub
       M.U0 = U;
       M.U1 = U + (long long)N * N;
       M.err = derr;
+      // algorithmic flops: both moments over the ordered pairs, 2 N^2 per (pair, c)
+      mark(1, 2.0 * 2.0 * (double)N * N * (double)n_in * (double)ordered);
       gemm6_kernel<MODE_MOMENT><<<tiles * M.nsplit, NTHREADS, SMEM_BYTES, s>>>(map_y, map_yw,
                                                                               map_y, M);
+      mark_end();
+      count_launch();
       cudaError_t e = cudaGetLastError();
       if (e != cudaSuccess) {
         err = std::string("tcgen05 kernel launch: ") + cudaGetErrorString(e);
@@ -670,6 +708,14 @@ int mixed_build_moments_rotated(const double* Lxo, const double* Lxv, const doub
     err = std::string("mixed moment build: ") + cudaGetErrorString(e);
     return AGF2_ERR_CUDA;
   }
+  for (size_t i = 0; i < ev_kind.size(); ++i) {
+    float ms = 0.f;
+    cudaEventElapsedTime(&ms, evs[2 * i], evs[2 * i + 1]);
+    stats->launches[ev_kind[i]] += 1;
+    stats->ms[ev_kind[i]] += ms;
+    stats->flops[ev_kind[i]] += ev_flops[i];
+  }
+  for (auto e2 : evs) cudaEventDestroy(e2);
   if (herr == DEV_TIMEOUT) {
     err = "tcgen05 pipeline wait timed out";
     return AGF2_ERR_TIMEOUT;

@@ -11,7 +11,7 @@ def declared_symbols():
     names = set()
     for hdr in (ROOT / "include").glob("*.h"):
         text = re.sub(r"/\*.*?\*/", "", hdr.read_text(), flags=re.S)
-        for m in re.finditer(r"^\s*(?:const\s+)?(?:int|void|char\s*\*|double)\s*\*?\s*(agf2_\w+)\s*\(",
+        for m in re.finditer(r"^\s*(?:const\s+)?(?:int|void|char\s*\*|double|long\s+long)\s*\*?\s*(agf2_\w+)\s*\(",
                              text, flags=re.M):
             names.add(m.group(1))
     return names
