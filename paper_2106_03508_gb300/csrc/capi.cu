@@ -12,6 +12,7 @@
 #include <chrono>
 #include <cmath>
 #include <cstdio>
+#include <cstdlib>
 #include <cstring>
 #include <map>
 #include <string>
@@ -571,6 +572,15 @@ struct FockOut {
   double mu, nerr;
 };
 
+bool trace_on() {
+  static int on = -1;
+  if (on < 0) {
+    const char* v = std::getenv("AGF2_TRACE");
+    on = (v && v[0] && v[0] != '0') ? 1 : 0;
+  }
+  return on == 1;
+}
+
 // Fock loop: see agf2_fock_loop in agf2.h.  F_in holds the initial F[D] on
 // entry; on exit D, F (= F[D]), e_qmo, C_qmo are written.
 FockOut fock_loop_impl(agf2_context* ctx, const double* h, const double* L, int naux, int nmo,
@@ -592,9 +602,12 @@ FockOut fock_loop_impl(agf2_context* ctx, const double* h, const double* L, int 
   int nh = 0, head = 0;  // ring buffer of history entries
   std::vector<int> order;
   FockOut out{0, 0, 0, 0, 0.0, 0.0};
+  const bool tr = trace_on();
   for (int cyc = 1; cyc <= o.max_cycle; ++cyc) {
     out.cycles = cyc;
+    auto tc0 = std::chrono::steady_clock::now();
     Shift sh = solve_shift(ctx, Fin, E, v, nmo, nse, nelec, o.shift_tol);
+    const double t_shift = seconds_since(tc0);
     out.evals += sh.evals;
     out.nerr = sh.nerr;
     CK(add_scalar(E, sh.delta, nse, s));
@@ -620,9 +633,15 @@ FockOut fock_loop_impl(agf2_context* ctx, const double* h, const double* L, int 
       g.alpha = 2.0;
       CK(dgemm(g, s));
     }
+    auto tf0 = std::chrono::steady_clock::now();
     fock_cocc(ctx, h, L, naux, nmo, Cocc, ab.k, Fout);
     CK(max_abs_diff(Dn, D, nn, red + 512, red, s));
     const double dD = scalar(ctx, red + 512);
+    if (tr)
+      std::fprintf(stderr, "[agf2] fock cycle %d: shift evals %d (%.1f ms) delta %.3e nerr %.2e k %d "
+                           "dD %.3e fock build %.1f ms cycle %.1f ms\n",
+                   cyc, sh.evals, 1e3 * t_shift, sh.delta, sh.nerr, ab.k, dD,
+                   1e3 * seconds_since(tf0), 1e3 * seconds_since(tc0));
     CK(cudaMemcpyAsync(D, Dn, nn * sizeof(double), cudaMemcpyDeviceToDevice, s));
     if (dD < o.tol_D) {
       out.converged = 1;
