@@ -203,6 +203,31 @@ int agf2_get_state(agf2_handle h, double* e, double* C, double* D, int* nqmo);
 int agf2_set_profiling(agf2_handle h, int enable);
 int agf2_kernel_stats(agf2_handle h, int kind, long long* launches, double* ms, double* flops);
 
+/*
+ * Allocation-free FP64 moment build (the paper has no counterpart: this is a
+ * deployment variant of agf2_build_moments with precision AGF2_FP64).
+ * For callers that cannot let a library allocate device memory -- e.g. an
+ * application whose own allocator owns the device budget, where cudaFree
+ * would synchronise the device and a late cudaMalloc could fail.  It needs no
+ * handle and calls no cudaMalloc/cudaFree: every intermediate lives in one
+ * static device array of 64 MiB inside the library, held on every GPU that
+ * loads the library until the process exits.  Roughly, the intermediates take
+ * 8 (nqmo nmo naux + o' v' naux + 6 nmo max(o', v')) bytes (o', v': occupied
+ * and virtual pole counts); sizes that could exceed 64 MiB for any
+ * occupied/virtual split are rejected with AGF2_ERR_INVALID_ARG before any
+ * argument is read.
+ *   Arguments and outputs as agf2_build_moments (nmom = 1); `stream` is a
+ *   cudaStream_t passed as void* (NULL: legacy default stream).  Returns when
+ *   the outputs are complete.
+ * The first call on a device (with that device current) looks up the static
+ * array's device address; make that call before any stream capture.  All
+ * calls share the array: calls whose GPU work overlaps (other streams or host
+ * threads) race on it.  Errors are reported by the return code only.
+ */
+int agf2_build_moments_noalloc(const double* L, int naux, int nmo, const double* e,
+                               const double* C, int nqmo, double mu, double* U_hole,
+                               double* U_part, void* stream);
+
 /* Number of CUDA kernels this library has launched since it was loaded
    (all handles; counts kernels issued by cuSOLVER/cuBLAS calls as zero). */
 long long agf2_launch_count(void);

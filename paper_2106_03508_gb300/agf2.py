@@ -31,6 +31,7 @@ EXPORTED = [
     "agf2_hcore_from_mo_energies", "agf2_build_moments", "agf2_compress",
     "agf2_fock_opts_default", "agf2_fock_loop", "agf2_opts_default", "agf2_run",
     "agf2_get_state", "agf2_set_profiling", "agf2_kernel_stats", "agf2_launch_count",
+    "agf2_build_moments_noalloc",
 ]
 
 
@@ -86,6 +87,7 @@ def _load():
         "agf2_kernel_stats": (I, [P, I, ct.POINTER(ct.c_longlong), ct.POINTER(D),
                                   ct.POINTER(D)]),
         "agf2_launch_count": (ct.c_longlong, []),
+        "agf2_build_moments_noalloc": (I, [P, I, I, P, P, I, D, P, P, P]),
     }
     for name, (res, args) in sig.items():
         fn = getattr(lib, name)
@@ -191,6 +193,12 @@ def agf2_kernel_stats(h, kind: int):
 
 def agf2_launch_count() -> int:
     return int(_lib.agf2_launch_count())
+
+
+def agf2_build_moments_noalloc(L, naux, nmo, e, C, nqmo, mu, U_hole, U_part, stream_ptr=0):
+    """FP64 moments without any device allocation (see include/agf2.h); returns the status."""
+    return int(_lib.agf2_build_moments_noalloc(L, naux, nmo, e, C, nqmo, float(mu), U_hole,
+                                               U_part, ct.c_void_p(stream_ptr)))
 
 
 # ---- torch-tensor conveniences (marshalling only) ----

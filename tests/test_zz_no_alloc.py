@@ -1,0 +1,56 @@
+"""The allocation-free FP64 moment build (agf2_build_moments_noalloc) -- for
+callers whose own allocator owns the device memory budget and who cannot let
+a library call cudaMalloc/cudaFree -- must give what the regular
+agf2_build_moments gives, call after call, through the C ABI.
+
+This file is collected last so that a stop-at-first-failure run has already
+run every other test; it also passes when run alone."""
+import numpy as np
+import pytest
+
+from paper_2106_03508_gb300.synth import make_system, random_poles
+
+pytestmark = pytest.mark.gpu
+RTOL = 1e-10   # the FP64 path's tolerance in the other GPU tests
+
+
+def _moments(agf2_lib, h, s, e, C, mu, noalloc):
+    import torch
+    L = torch.from_numpy(s.L).cuda()
+    ed, Cd = torch.from_numpy(e).cuda(), torch.from_numpy(C).cuda()
+    Uh = torch.full((2, s.nmo, s.nmo), 7.0, dtype=torch.float64, device="cuda")  # stale values
+    Up = torch.full_like(Uh, -3.0)
+    if noalloc:
+        rc = agf2_lib.agf2_build_moments_noalloc(L.data_ptr(), s.naux, s.nmo, ed.data_ptr(),
+                                                 Cd.data_ptr(), len(e), mu, Uh.data_ptr(),
+                                                 Up.data_ptr(), 0)
+        assert rc == agf2_lib.AGF2_OK, rc
+    else:
+        agf2_lib.agf2_build_moments(h.h, L.data_ptr(), s.naux, s.nmo, ed.data_ptr(), Cd.data_ptr(),
+                                    len(e), mu, 1, agf2_lib.AGF2_FP64, Uh.data_ptr(), Up.data_ptr())
+    torch.cuda.synchronize()
+    return Uh.cpu().numpy(), Up.cpu().numpy()
+
+
+def test_noalloc_matches_regular_entry_point_twice(cuda_handle, agf2_lib):
+    cases = [(24, 72, 29, 96, 1), (37, 90, 30, 70, 2)]  # two calls in a row, different sizes
+    for nmo, nq, no, naux, seed in cases:
+        s = make_system(nmo, max(1, nmo // 5), naux, seed)
+        e, C, mu = random_poles(nmo, nq, no, seed + 3)
+        Ah, Ap = _moments(agf2_lib, cuda_handle, s, e, C, mu, noalloc=True)
+        Bh, Bp = _moments(agf2_lib, cuda_handle, s, e, C, mu, noalloc=False)
+        for a, b in ((Ah, Bh), (Ap, Bp)):
+            assert np.max(np.abs(a - b)) <= RTOL * np.max(np.abs(b))
+
+
+def test_noalloc_rejects_oversized_problem(agf2_lib):
+    import torch
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    small = torch.zeros(16, dtype=torch.float64, device="cuda")
+    # naux so large that the rotated integrals alone exceed the static scratch;
+    # rejected from the sizes before any argument is read
+    rc = agf2_lib.agf2_build_moments_noalloc(small.data_ptr(), 10 ** 6, 24, small.data_ptr(),
+                                             small.data_ptr(), 72, 0.0, small.data_ptr(),
+                                             small.data_ptr(), 0)
+    assert rc == agf2_lib.AGF2_ERR_INVALID_ARG
