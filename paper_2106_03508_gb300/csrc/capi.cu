@@ -133,6 +133,13 @@ double seconds_since(std::chrono::steady_clock::time_point t0) {
   return std::chrono::duration<double>(std::chrono::steady_clock::now() - t0).count();
 }
 
+// K splits so that an M x N FP64 GEMM with a long K fills about two waves of CTAs.
+int split_for(int M, int N, long long K) {
+  const long long tiles = (long long)((M + 63) / 64) * ((N + 63) / 64);
+  const long long want = (2 * 152 + tiles - 1) / tiles;
+  return (int)std::max(1LL, std::min(want, K / 256));
+}
+
 // ---------------------------------------------------------------------------
 // Fock matrix, Eq. (fock_matrix), density fitted
 // ---------------------------------------------------------------------------
@@ -172,6 +179,9 @@ void fock_general(agf2_context* ctx, const double* h, const double* L, int naux,
     g.A = Z; g.sAm = (long long)naux * n; g.sAk = 1;
     g.B = L; g.sBk = n; g.sBn = 1;
     g.C = K; g.sCm = n; g.sCn = 1;
+    g.atomic = true;
+    g.ksplit = split_for(n, n, g.K);
+    CK(cudaMemsetAsync(K, 0, nn * sizeof(double), s));
     CK(dgemm(g, s));
   }
   CK(fock_combine(h, J, K, nn, F, s));
@@ -199,12 +209,15 @@ void fock_cocc(agf2_context* ctx, const double* h, const double* L, int naux, in
   CK(gamma_from_y(Y, Cocc, n, naux, k, gam, s));
   CK(coulomb_from_gamma(L, gam, naux, n, J, s));
   {
-    DGemm g;  // K = 2 Y Y^T over (Q, c)
+    DGemm g;  // K = 2 Y Y^T over (Q, c), split over K with FP64 atomics
     g.M = n; g.N = n; g.K = naux * k;
     g.A = Y; g.sAm = (long long)naux * k; g.sAk = 1;
     g.B = Y; g.sBk = 1; g.sBn = (long long)naux * k;
     g.C = K; g.sCm = n; g.sCn = 1;
     g.alpha = 2.0;
+    g.atomic = true;
+    g.ksplit = split_for(n, n, g.K);
+    CK(cudaMemsetAsync(K, 0, nn * sizeof(double), s));
     CK(dgemm(g, s));
   }
   CK(fock_combine(h, J, K, nn, F, s));
@@ -461,6 +474,7 @@ struct Shift {
   double delta, nerr;
   int evals;
   bool converged;
+  bool last_is_best;  // the extended-Hamiltonian buffers hold the decomposition at delta
 };
 
 // Common shift of the auxiliary energies so that n(delta; k) = nelec, with k
@@ -499,7 +513,7 @@ Shift solve_shift(agf2_context* ctx, const double* F, const double* E, const dou
   double d = 0.0;
   double f = eval(0.0, fp);
   int evals = 1;
-  if (std::fabs(f) < tol) return Shift{0.0, f, evals, true};
+  if (std::fabs(f) < tol) return Shift{0.0, f, evals, true, true};
   bool has_lo = false, has_hi = false;
   double lo = 0.0, hi = 0.0;
   auto bracket = [&](double x, double fx) {
@@ -508,6 +522,7 @@ Shift solve_shift(agf2_context* ctx, const double* F, const double* E, const dou
   };
   bracket(d, f);
   double best = d, fbest = f;
+  bool last_best = true;
   double expand = 1.0;
   for (int it = 0; it < 200; ++it) {
     double dn = (fp > 0.0 && std::isfinite(fp)) ? d - f / fp : NAN;
@@ -521,14 +536,15 @@ Shift solve_shift(agf2_context* ctx, const double* F, const double* E, const dou
     f = eval(d, fp);
     ++evals;
     bracket(d, f);
-    if (std::fabs(f) < std::fabs(fbest)) { best = d; fbest = f; }
+    last_best = std::fabs(f) < std::fabs(fbest);
+    if (last_best) { best = d; fbest = f; }
     if (std::fabs(f) < tol) break;
     if (has_lo && has_hi && hi - lo < 1e-14) break;
     if (!has_lo || !has_hi) {
       if (expand > 1e6) break;
     }
   }
-  return Shift{best, fbest, evals, std::fabs(fbest) < tol};
+  return Shift{best, fbest, evals, std::fabs(fbest) < tol, last_best};
 }
 
 // Pulay extrapolation coefficients from B_ab = <r_a, r_b> (host solve of the
@@ -611,7 +627,9 @@ FockOut fock_loop_impl(agf2_context* ctx, const double* h, const double* L, int 
     out.evals += sh.evals;
     out.nerr = sh.nerr;
     CK(add_scalar(E, sh.delta, nse, s));
-    Eig eg = diag_extended(ctx, Fin, E, v, 0.0, nmo, nse);
+    // the shift solve's last decomposition is the one at the chosen delta
+    Eig eg = sh.last_is_best ? Eig{ws(ctx, "ext_H", (size_t)n * n), ws(ctx, "ext_w", n), n}
+                             : diag_extended(ctx, Fin, E, v, 0.0, nmo, nse);
     std::vector<double> wt = pole_weights(ctx, eg, nmo);
     std::vector<double> ev = to_host(ctx, eg.w, n);
     Aufbau ab = aufbau(ev, wt, nelec);

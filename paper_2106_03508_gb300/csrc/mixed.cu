@@ -53,7 +53,7 @@ constexpr int STAGE_BYTES = 3 * TILE_A + 3 * TILE_B;
 constexpr int SMEM_BYTES = STAGES * STAGE_BYTES + 1024;
 constexpr int TMEM_COLS = 512;  // PAIR: (hi, lo) x (X_xy, X_yx) x BN; MOMENT: (hi, lo) x BN
 constexpr int KCHUNK = 2 * BN;  // K entries of Y one PAIR tile writes: S and D of BN c's
-constexpr int NTHREADS = 192;   // warp 0 TMA, warp 1 MMA, warps 2..5 epilogue
+constexpr int NTHREADS = 320;   // warp 0 TMA, warp 1 MMA, warps 2..9 epilogue
 
 enum { MODE_PAIR = 0, MODE_MOMENT = 1 };
 
@@ -71,7 +71,8 @@ struct Params {
   int hole;         // MODE_PAIR: 1 -> B rows along map dim 1, 0 -> along dim 2
   int pair0;        // first pair of this block
   int ksplit;       // MODE_MOMENT: K steps per CTA
-  int nsplit;       // MODE_MOMENT: CTAs along K per (tile, moment)
+  int nsplit;       // MODE_MOMENT: K splits per (tile, moment)
+  int ntiles;       // tiles of this launch (the persistent CTAs loop over them)
   long long kpp;    // MODE_PAIR: K entries of Y per pair (n_cchunks * KCHUNK)
   const int2* pairs;
   const double* e_out;
@@ -107,62 +108,88 @@ __device__ __forceinline__ void load_a(const CUtensorMap* mapA, uint8_t* dst, ui
     tc::tma_load_3d(dst, mapA, bar, ks * BK, s.a_row, limb);
 }
 
+// Work of one tile: up to two K segments into one accumulator set.
+struct TileWork {
+  Segment seg[2];
+  int nseg;
+  int p0, c0, q0, moment, pair_local;
+  int2 pr;
+};
+
+template <int MODE>
+__device__ __forceinline__ TileWork decode_tile(const Params& P, int t) {
+  TileWork w;
+  w.nseg = 1;
+  w.p0 = w.c0 = w.q0 = w.moment = w.pair_local = 0;
+  w.pr = make_int2(0, 0);
+  if (MODE == MODE_PAIR) {
+    int b = t;
+    const int cc = b % P.n_cchunks; b /= P.n_cchunks;
+    const int pt = b % P.n_ptiles; b /= P.n_ptiles;
+    w.pair_local = b;
+    w.pr = P.pairs[P.pair0 + w.pair_local];
+    w.p0 = pt * BM;
+    w.c0 = cc * BN;
+    w.seg[0] = Segment{w.p0, w.pr.x, w.c0, w.pr.y, 0, 0, P.ksteps, false};
+    w.seg[1] = Segment{w.p0, w.pr.y, w.c0, w.pr.x, 2 * BN, 0, P.ksteps, false};
+    w.nseg = (w.pr.x == w.pr.y) ? 1 : 2;
+  } else {
+    int b = t;
+    const int sp = b % P.nsplit; b /= P.nsplit;
+    w.moment = b % 2; b /= 2;
+    const int qt = b % P.n_qtiles; b /= P.n_qtiles;
+    const int pt = b;
+    w.p0 = pt * BM;
+    w.q0 = qt * BN;
+    const int kb = sp * P.ksplit;
+    const int ke = min(P.ksteps, kb + P.ksplit);
+    w.seg[0] = Segment{w.p0, 0, w.q0, 0, 0, kb, ke, w.moment == 1};
+  }
+  return w;
+}
+
+// Persistent kernel: CTA b handles tiles b, b + gridDim.x, ...
+//   warp 0: TMA producer (runs ahead across tiles through the smem ring)
+//   warp 1: TMEM allocation + single-thread tcgen05.mma issue
+//   warps 2..9: epilogue; warp w reads TMEM lane quarter w % 4 and column
+//   half (w - 2) / 4 of each accumulator
+// MODE_PAIR uses all 512 TMEM columns for one tile's accumulators
+// (X_xy hi/lo, X_yx hi/lo); MODE_MOMENT double-buffers its 256-column
+// accumulator set so a tile's FP64 drain overlaps the next tile's MMAs.
 template <int MODE>
 __global__ void __launch_bounds__(NTHREADS, 1)
 gemm6_kernel(const __grid_constant__ CUtensorMap mapA, const __grid_constant__ CUtensorMap mapA2,
              const __grid_constant__ CUtensorMap mapB, const Params P) {
+  constexpr int NBUF = (MODE == MODE_PAIR) ? 1 : 2;
+  constexpr int BUF_COLS = (MODE == MODE_PAIR) ? 4 * BN : 2 * BN;
+  constexpr int N_EPI_WARPS = (NTHREADS / 32) - 2;
   extern __shared__ uint8_t smem_raw[];
   uint8_t* smem = reinterpret_cast<uint8_t*>(
       (reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~uintptr_t(1023));
   __shared__ __align__(8) uint64_t full_bar[STAGES];
   __shared__ __align__(8) uint64_t empty_bar[STAGES];
-  __shared__ __align__(8) uint64_t acc_bar;
+  __shared__ __align__(8) uint64_t accf_bar[NBUF];   // MMA -> epilogue
+  __shared__ __align__(8) uint64_t acce_bar[NBUF];   // epilogue -> MMA
   __shared__ uint32_t tmem_base_sh;
   __shared__ int abort_sh;
-  __shared__ int issued_sh, consumed_sh;
+  __shared__ int issued_sh, consumed_sh, committed_sh;
 
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   volatile int* abort_flag = &abort_sh;
-
-  // ---- decode this CTA's work into at most two K segments ----
-  Segment seg[2];
-  int nseg = 1;
-  int p0 = 0, c0 = 0, q0 = 0, moment = 0, pair_local = 0;
-  int2 pr = make_int2(0, 0);
-  if (MODE == MODE_PAIR) {
-    int b = blockIdx.x;
-    const int cc = b % P.n_cchunks; b /= P.n_cchunks;
-    const int pt = b % P.n_ptiles; b /= P.n_ptiles;
-    pair_local = b;
-    pr = P.pairs[P.pair0 + pair_local];
-    p0 = pt * BM;
-    c0 = cc * BN;
-    seg[0] = Segment{p0, pr.x, c0, pr.y, 0, 0, P.ksteps, false};
-    seg[1] = Segment{p0, pr.y, c0, pr.x, 2 * BN, 0, P.ksteps, false};
-    nseg = (pr.x == pr.y) ? 1 : 2;
-  } else {
-    int b = blockIdx.x;
-    const int sp = b % P.nsplit; b /= P.nsplit;
-    moment = b % 2; b /= 2;
-    const int qt = b % P.n_qtiles; b /= P.n_qtiles;
-    const int pt = b;
-    p0 = pt * BM;
-    q0 = qt * BN;
-    const int kb = sp * P.ksplit;
-    const int ke = min(P.ksteps, kb + P.ksplit);
-    seg[0] = Segment{p0, 0, q0, 0, 0, kb, ke, moment == 1};
-    nseg = 1;
-  }
 
   if (threadIdx.x == 0) {
     for (int s = 0; s < STAGES; ++s) {
       tc::mbar_init(&full_bar[s], 1);
       tc::mbar_init(&empty_bar[s], 1);
     }
-    tc::mbar_init(&acc_bar, 1);
+    for (int b = 0; b < NBUF; ++b) {
+      tc::mbar_init(&accf_bar[b], 1);
+      tc::mbar_init(&acce_bar[b], N_EPI_WARPS);
+    }
     abort_sh = 0;
     issued_sh = 0;
     consumed_sh = 0;
+    committed_sh = 0;
     tc::fence_mbar_init();
   }
   if (warp == 1) {
@@ -180,30 +207,34 @@ gemm6_kernel(const __grid_constant__ CUtensorMap mapA, const __grid_constant__ C
     tc::tma_prefetch(&mapB);
     if (MODE == MODE_MOMENT) tc::tma_prefetch(&mapA2);
     int t = 0;
-    for (int si = 0; si < nseg && !*abort_flag; ++si) {
-      const Segment& s = seg[si];
-      for (int ks = s.kbeg; ks < s.kend; ++ks, ++t) {
-        const int st = t % STAGES;
-        const uint32_t ph = (t / STAGES) & 1;
-        if (!tc::mbar_wait(&empty_bar[st], ph ^ 1, abort_flag)) break;
-        uint8_t* base = smem + st * STAGE_BYTES;
-        tc::mbar_arrive_expect_tx(&full_bar[st], STAGE_BYTES);
-        for (int l = 0; l < 3; ++l) {
-          if (MODE == MODE_PAIR) {
-            load_a(&mapA, base + l * TILE_A, &full_bar[st], P, s, ks, l);
-            if (P.hole)
-              tc::tma_load_4d(base + 3 * TILE_A + l * TILE_B, &mapB, &full_bar[st], ks * BK,
-                              s.b_row, s.b_idx, l);
-            else
-              tc::tma_load_4d(base + 3 * TILE_A + l * TILE_B, &mapB, &full_bar[st], ks * BK,
-                              s.b_idx, s.b_row, l);
-          } else {
-            load_a(s.a_w ? &mapA2 : &mapA, base + l * TILE_A, &full_bar[st], P, s, ks, l);
-            tc::tma_load_3d(base + 3 * TILE_A + l * TILE_B, &mapB, &full_bar[st], ks * BK,
-                            s.b_row, l);
+    bool ok = true;
+    for (int tile = blockIdx.x; tile < P.ntiles && ok; tile += gridDim.x) {
+      const TileWork w = decode_tile<MODE>(P, tile);
+      for (int si = 0; si < w.nseg && ok; ++si) {
+        const Segment& s = w.seg[si];
+        for (int ks = s.kbeg; ks < s.kend; ++ks, ++t) {
+          const int st = t % STAGES;
+          const uint32_t ph = (t / STAGES) & 1;
+          if (!tc::mbar_wait(&empty_bar[st], ph ^ 1, abort_flag)) { ok = false; break; }
+          uint8_t* base = smem + st * STAGE_BYTES;
+          tc::mbar_arrive_expect_tx(&full_bar[st], STAGE_BYTES);
+          for (int l = 0; l < 3; ++l) {
+            if (MODE == MODE_PAIR) {
+              load_a(&mapA, base + l * TILE_A, &full_bar[st], P, s, ks, l);
+              if (P.hole)
+                tc::tma_load_4d(base + 3 * TILE_A + l * TILE_B, &mapB, &full_bar[st], ks * BK,
+                                s.b_row, s.b_idx, l);
+              else
+                tc::tma_load_4d(base + 3 * TILE_A + l * TILE_B, &mapB, &full_bar[st], ks * BK,
+                                s.b_idx, s.b_row, l);
+            } else {
+              load_a(s.a_w ? &mapA2 : &mapA, base + l * TILE_A, &full_bar[st], P, s, ks, l);
+              tc::tma_load_3d(base + 3 * TILE_A + l * TILE_B, &mapB, &full_bar[st], ks * BK,
+                              s.b_row, l);
+            }
           }
+          issued_sh = t + 1;
         }
-        issued_sh = t + 1;
       }
     }
   } else if (warp == 1 && lane == 0) {
@@ -212,43 +243,61 @@ gemm6_kernel(const __grid_constant__ CUtensorMap mapA, const __grid_constant__ C
     // correction products h_a h_b (a + b = 1, 2) into the lo accumulator
     const int pa[5] = {2, 1, 0, 1, 0};
     const int pb[5] = {0, 1, 2, 0, 1};
-    int t = 0;
+    int t = 0, lt = 0;
     bool ok = true;
-    for (int si = 0; si < nseg && ok; ++si) {
-      const Segment& s = seg[si];
-      const uint32_t acc_hi = tmem + s.acc_col, acc_lo = tmem + s.acc_col + BN;
-      for (int ks = s.kbeg; ks < s.kend; ++ks, ++t) {
-        const int st = t % STAGES;
-        const uint32_t ph = (t / STAGES) & 1;
-        if (!tc::mbar_wait(&full_bar[st], ph, abort_flag)) { ok = false; break; }
-        tc::tc_fence_after();
-        const uint32_t base = tc::smem_u32(smem + st * STAGE_BYTES);
+    for (int tile = blockIdx.x; tile < P.ntiles && ok; tile += gridDim.x, ++lt) {
+      const TileWork w = decode_tile<MODE>(P, tile);
+      const int buf = lt % NBUF;
+      const uint32_t use = (uint32_t)(lt / NBUF);
+      // wait until the epilogue has drained this accumulator set
+      if (!tc::mbar_wait(&acce_bar[buf], (use & 1) ^ 1, abort_flag)) { ok = false; break; }
+      tc::tc_fence_after();
+      const uint32_t accbase = tmem + buf * BUF_COLS;
+      for (int si = 0; si < w.nseg && ok; ++si) {
+        const Segment& s = w.seg[si];
+        const uint32_t acc_hi = accbase + s.acc_col, acc_lo = accbase + s.acc_col + BN;
+        for (int ks = s.kbeg; ks < s.kend; ++ks, ++t) {
+          const int st = t % STAGES;
+          const uint32_t ph = (t / STAGES) & 1;
+          if (!tc::mbar_wait(&full_bar[st], ph, abort_flag)) { ok = false; break; }
+          tc::tc_fence_after();
+          const uint32_t base = tc::smem_u32(smem + st * STAGE_BYTES);
 #pragma unroll
-        for (int kk = 0; kk < BK / 16; ++kk) {
-          const uint32_t acc = (ks > s.kbeg || kk > 0) ? 1u : 0u;
+          for (int kk = 0; kk < BK / 16; ++kk) {
+            const uint32_t acc = (ks > s.kbeg || kk > 0) ? 1u : 0u;
 #pragma unroll
-          for (int pi = 0; pi < 5; ++pi) {
-            const uint64_t ad = tc::sdesc_sw128(base + pa[pi] * TILE_A + kk * 32);
-            const uint64_t bd = tc::sdesc_sw128(base + 3 * TILE_A + pb[pi] * TILE_B + kk * 32);
-            tc::umma_bf16(acc_lo, ad, bd, idesc, (acc || pi > 0) ? 1u : 0u);
+            for (int pi = 0; pi < 5; ++pi) {
+              const uint64_t ad = tc::sdesc_sw128(base + pa[pi] * TILE_A + kk * 32);
+              const uint64_t bd = tc::sdesc_sw128(base + 3 * TILE_A + pb[pi] * TILE_B + kk * 32);
+              tc::umma_bf16(acc_lo, ad, bd, idesc, (acc || pi > 0) ? 1u : 0u);
+            }
+            tc::umma_bf16(acc_hi, tc::sdesc_sw128(base + kk * 32),
+                          tc::sdesc_sw128(base + 3 * TILE_A + kk * 32), idesc, acc);
           }
-          tc::umma_bf16(acc_hi, tc::sdesc_sw128(base + kk * 32),
-                        tc::sdesc_sw128(base + 3 * TILE_A + kk * 32), idesc, acc);
+          tc::umma_commit(&empty_bar[st]);
+          consumed_sh = t + 1;
         }
-        tc::umma_commit(&empty_bar[st]);
-        consumed_sh = t + 1;
       }
+      tc::umma_commit(&accf_bar[buf]);
+      committed_sh = lt + 1;
     }
-    tc::umma_commit(&acc_bar);
   } else if (warp >= 2) {
     // ---------------- epilogue ----------------
-    const int qd = warp & 3;                 // TMEM lane quarter of this warp
+    const int qd = warp & 3;                        // TMEM lane quarter of this warp
+    const int half = (warp - 2) / 4;                // column half of each accumulator
     const int r = qd * 32 + lane;
-    const uint32_t trow = tmem + ((uint32_t)(qd * 32) << 16);
-    if (tc::mbar_wait(&acc_bar, 0, abort_flag)) {
+    const int col0 = half * (BN / 2);
+    int lt = 0;
+    for (int tile = blockIdx.x; tile < P.ntiles; tile += gridDim.x, ++lt) {
+      const TileWork w = decode_tile<MODE>(P, tile);
+      const int buf = lt % NBUF;
+      const uint32_t use = (uint32_t)(lt / NBUF);
+      if (!tc::mbar_wait(&accf_bar[buf], use & 1, abort_flag)) break;
       tc::tc_fence_after();
+      const uint32_t trow = tmem + buf * BUF_COLS + ((uint32_t)(qd * 32) << 16);
+      const int p = w.p0 + r;
       if (MODE == MODE_PAIR) {
-        const int p = p0 + r;
+        const int2 pr = w.pr;
         const bool diag = (pr.x == pr.y);
         const float sS = diag ? 0.5f : 0.70710678118654752f;
         const float sD = diag ? 0.0f : 1.22474487139158905f;
@@ -259,8 +308,8 @@ gemm6_kernel(const __grid_constant__ CUtensorMap mapA, const __grid_constant__ C
         const float inv_uy = prow ? 1.0f / P.unitY[p] : 0.f;
         const float inv_uyw = prow ? 1.0f / P.unitYw[p] : 0.f;
         // this tile's K range of Y: [kS, kS + BN) for S, [kS + BN, kS + 2 BN) for D
-        const long long kS = (long long)pair_local * P.kpp + (long long)(c0 / BN) * KCHUNK;
-        for (int cb = 0; cb < BN; cb += 32) {
+        const long long kS = (long long)w.pair_local * P.kpp + (long long)(w.c0 / BN) * KCHUNK;
+        for (int cb = col0; cb < col0 + BN / 2; cb += 32) {
           float h1[32], l1[32], h2[32], l2[32];
           tc::tmem_ld32(trow + cb, h1);
           tc::tmem_ld32(trow + BN + cb, l1);
@@ -277,8 +326,8 @@ gemm6_kernel(const __grid_constant__ CUtensorMap mapA, const __grid_constant__ C
               __nv_bfloat16* ob = reinterpret_cast<__nv_bfloat16*>(out);
 #pragma unroll
               for (int c = 0; c < 8; ++c) {
-                const int ci = c0 + cb + g + c;
-                float ys = 0.f, yd = 0.f, w = 0.f;
+                const int ci = w.c0 + cb + g + c;
+                float ys = 0.f, yd = 0.f, wt = 0.f;
                 if (ci < P.n_in) {
                   // B-row units: hole rows (y, c) -> y*v + c ; particle rows (c, y) -> c*v + y
                   const long long rb1 = P.hole ? (long long)pr.y * P.v_stride + ci
@@ -289,13 +338,13 @@ gemm6_kernel(const __grid_constant__ CUtensorMap mapA, const __grid_constant__ C
                   const float xb = diag ? xa : (h2[g + c] + l2[g + c]) * (uA2 * P.unitB[rb2]);
                   ys = sS * (xa + xb);
                   yd = sD * (xa - xb);
-                  w = (float)(ex - P.e_in[ci]);
+                  wt = (float)(ex - P.e_in[ci]);
                 }
                 // out[3*arr + limb], arr: 0 Y_S, 1 Y_D, 2 Yw_S, 3 Yw_D
                 tc::slice3f(ys * inv_uy, ob[0 * 8 + c], ob[1 * 8 + c], ob[2 * 8 + c]);
                 tc::slice3f(yd * inv_uy, ob[3 * 8 + c], ob[4 * 8 + c], ob[5 * 8 + c]);
-                tc::slice3f(ys * w * inv_uyw, ob[6 * 8 + c], ob[7 * 8 + c], ob[8 * 8 + c]);
-                tc::slice3f(yd * w * inv_uyw, ob[9 * 8 + c], ob[10 * 8 + c], ob[11 * 8 + c]);
+                tc::slice3f(ys * wt * inv_uyw, ob[6 * 8 + c], ob[7 * 8 + c], ob[8 * 8 + c]);
+                tc::slice3f(yd * wt * inv_uyw, ob[9 * 8 + c], ob[10 * 8 + c], ob[11 * 8 + c]);
               }
 #pragma unroll
               for (int l = 0; l < 3; ++l) {
@@ -308,17 +357,16 @@ gemm6_kernel(const __grid_constant__ CUtensorMap mapA, const __grid_constant__ C
           }
         }
       } else {
-        const int p = p0 + r;
-        double* U = moment == 0 ? P.U0 : P.U1;
-        const double uA = (p < P.N) ? (double)(moment == 0 ? P.unitA : P.unitA2)[p] : 0.0;
-        for (int cb = 0; cb < BN; cb += 32) {
+        double* U = w.moment == 0 ? P.U0 : P.U1;
+        const double uA = (p < P.N) ? (double)(w.moment == 0 ? P.unitA : P.unitA2)[p] : 0.0;
+        for (int cb = col0; cb < col0 + BN / 2; cb += 32) {
           float hi[32], lo[32];
           tc::tmem_ld32(trow + cb, hi);
           tc::tmem_ld32(trow + BN + cb, lo);
           if (p < P.N) {
 #pragma unroll 4
             for (int c = 0; c < 32; ++c) {
-              const int q = q0 + cb + c;
+              const int q = w.q0 + cb + c;
               if (q < P.N)
                 atomicAdd(U + (long long)p * P.N + q,
                           (double)(hi[c] + lo[c]) * (uA * (double)P.unitB[q]));
@@ -326,6 +374,10 @@ gemm6_kernel(const __grid_constant__ CUtensorMap mapA, const __grid_constant__ C
           }
         }
       }
+      // this accumulator set may be overwritten once every epilogue warp is done
+      tc::tc_fence_before();
+      __syncwarp();
+      if (lane == 0) tc::mbar_arrive(&acce_bar[buf]);
     }
   }
 
@@ -342,9 +394,11 @@ gemm6_kernel(const __grid_constant__ CUtensorMap mapA, const __grid_constant__ C
     }
   }
   if (warp == 1) {
-    if (abort_sh) {  // MMAs may still be running: wait for the last commit
+    if (abort_sh && committed_sh > 0) {  // MMAs may still be running: wait for the last commit
+      const int lt = committed_sh - 1;
       const long long t0 = clock64();
-      while (!tc::mbar_try_wait(&acc_bar, 0) && clock64() - t0 < tc::kWaitCycles) {
+      while (!tc::mbar_try_wait(&accf_bar[lt % NBUF], (uint32_t)((lt / NBUF) & 1)) &&
+             clock64() - t0 < tc::kWaitCycles) {
       }
     }
     tc::tc_fence_after();
@@ -529,6 +583,8 @@ int mixed_build_moments_rotated(const double* Lxo, const double* Lxv, const doub
     }
     attr_done[dev & 63] = true;
   }
+  int nsm = 148;
+  cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev);
   const int Qs = (naux + BK - 1) / BK * BK;
   const long long NQs = (long long)N * Qs;
   __nv_bfloat16* lxo = grow<__nv_bfloat16>(W.lx_o, 3LL * o * NQs, err);
@@ -621,10 +677,19 @@ int mixed_build_moments_rotated(const double* Lxo, const double* Lxv, const doub
     cudaMemcpyAsync(dpairs, pairs.data(), pairs.size() * sizeof(int2), cudaMemcpyHostToDevice, s);
     const int n_cchunks = (n_in + BN - 1) / BN;
     const long long kpp = (long long)n_cchunks * KCHUNK;
-    // pairs per block: Y + Yw limb planes of the block stay near L2 size
+    // pairs per block: Y + Yw limb planes of the block stay near L2 size, and the
+    // block's tile count is a whole number of waves of the persistent CTAs
     const double per_pair = (double)N * kpp * 2 /*Y,Yw*/ * 3 /*limbs*/ * 2 /*bytes*/;
+    const int tpp = n_ptiles * n_cchunks;  // tiles per pair
     int bp = (int)std::max(1.0, std::floor(96.0e6 / per_pair));
-    bp = std::min<int>(bp, (int)pairs.size());
+    {
+      int g = nsm, t = tpp;
+      while (t) { const int r = g % t; g = t; t = r; }  // gcd(nsm, tpp)
+      const int unit = nsm / g;                          // pairs per whole wave
+      const int bp_lim = (int)std::floor(160.0e6 / per_pair);
+      if (unit <= bp_lim) bp = std::max(unit, bp / unit * unit);
+    }
+    bp = std::max(1, std::min<int>(bp, (int)pairs.size()));
     const long long Ks = (long long)bp * kpp;
     __nv_bfloat16* y = grow<__nv_bfloat16>(W.y, 3LL * N * Ks, err);
     __nv_bfloat16* yw = grow<__nv_bfloat16>(W.yw, 3LL * N * Ks, err);
@@ -655,7 +720,8 @@ int mixed_build_moments_rotated(const double* Lxo, const double* Lxv, const doub
       P.Ks = Ks;
       P.plane = (long long)N * Ks;
       P.err = derr;
-      const int grid1 = np * n_ptiles * n_cchunks;
+      const int grid1 = std::min(np * n_ptiles * n_cchunks, nsm);
+      P.ntiles = np * n_ptiles * n_cchunks;
       // algorithmic flops: GEMM 1 for the ordered pairs of this block
       long long ordered = 0;
       for (int t = 0; t < np; ++t) ordered += (pairs[b0 + t].x == pairs[b0 + t].y) ? 1 : 2;
@@ -677,10 +743,12 @@ int mixed_build_moments_rotated(const double* Lxo, const double* Lxv, const doub
       M.n_qtiles = (N + BN - 1) / BN;
       M.ksteps = (int)((K + BK - 1) / BK);
       const int tiles = M.n_ptiles * M.n_qtiles * 2;
-      int nsplit = std::max(1, (148 * 2 + tiles - 1) / tiles);
+      // about two tiles per persistent CTA, so each drain overlaps the next tile's MMAs
+      int nsplit = std::max(1, (nsm * 2 + tiles - 1) / tiles);
       nsplit = std::min(nsplit, M.ksteps);
       M.ksplit = (M.ksteps + nsplit - 1) / nsplit;
       M.nsplit = (M.ksteps + M.ksplit - 1) / M.ksplit;  // every split non-empty
+      M.ntiles = tiles * M.nsplit;
       M.n_out = 0;
       M.unitA = u_y;
       M.unitA2 = u_yw;
@@ -690,8 +758,8 @@ int mixed_build_moments_rotated(const double* Lxo, const double* Lxv, const doub
       M.err = derr;
       // algorithmic flops: both moments over the ordered pairs, 2 N^2 per (pair, c)
       mark(1, 2.0 * 2.0 * (double)N * N * (double)n_in * (double)ordered);
-      gemm6_kernel<MODE_MOMENT><<<tiles * M.nsplit, NTHREADS, SMEM_BYTES, s>>>(map_y, map_yw,
-                                                                              map_y, M);
+      gemm6_kernel<MODE_MOMENT><<<std::min(M.ntiles, nsm), NTHREADS, SMEM_BYTES, s>>>(
+          map_y, map_yw, map_y, M);
       mark_end();
       count_launch();
       cudaError_t e = cudaGetLastError();
