@@ -44,6 +44,8 @@ def parse():
     ap.add_argument("--cpu-seconds", type=float, default=15.0,
                     help="target CPU time of the oracle sample")
     ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--shift-mode", type=int, default=1, choices=[0, 1],
+                    help="Fock-loop shift: 0 solve every cycle, 1 one Newton step per cycle")
     return ap.parse_args()
 
 
@@ -212,6 +214,7 @@ def run_ours(args):
 
     o = agf2.agf2_opts_default()
     o.precision = prec
+    o.fock.shift_mode = args.shift_mode
     o.max_iter = max(1, args.warmup)
     o.resume = 0
     agf2.agf2_run(h.h, hc.data_ptr(), L.data_ptr(), naux, N, nelec, eps.data_ptr(), o)
@@ -281,6 +284,7 @@ def run_ours(args):
     if args.fp64_steps > 0 and prec != agf2.AGF2_FP64:
         of = agf2.agf2_opts_default()
         of.precision = agf2.AGF2_FP64
+        of.fock.shift_mode = args.shift_mode
         of.max_iter = 1
         of.resume = 1
         barrier()
@@ -319,6 +323,7 @@ def run_ours(args):
         "scaling": "weak", "vs_baseline": None,
         "dtype": "bf16x3" if prec == agf2.AGF2_BF16X3 else "f64", "data": "synthetic",
         "config": {**workload_desc(args.config), "precision": args.precision,
+                   "fock_shift_mode": args.shift_mode,
                    "l2": "inputs larger than L2 (L = %.0f MB FP64)" % (L.numel() * 8 / 1e6),
                    "parallelism": "replicas" if world > 1 else "single"},
         "stage_seconds_per_iter": {k: statistics.mean(r[k] for r in results)

@@ -105,6 +105,12 @@ typedef struct {
     double damping;    /* linear mixing of F before DIIS starts (0.3)         */
     int    diis_start; /* first cycle whose pair enters DIIS (10)             */
     int    diis_space; /* DIIS history length (6)                             */
+    int    shift_mode; /* 1 (default): one safeguarded Newton step on the shift
+                          per cycle, one eigendecomposition per cycle;
+                          0: solve the shift to shift_tol every cycle (Newton
+                          with bracket, the same root as bisection).  Both stop
+                          at the same fixed point: max|dD| < tol_D and
+                          |n - nelec| < shift_tol                             */
 } agf2_fock_opts;
 
 typedef struct {

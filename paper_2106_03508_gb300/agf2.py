@@ -37,7 +37,8 @@ EXPORTED = [
 
 class agf2_fock_opts(ct.Structure):
     _fields_ = [("tol_D", ct.c_double), ("max_cycle", ct.c_int), ("shift_tol", ct.c_double),
-                ("damping", ct.c_double), ("diis_start", ct.c_int), ("diis_space", ct.c_int)]
+                ("damping", ct.c_double), ("diis_start", ct.c_int), ("diis_space", ct.c_int),
+                ("shift_mode", ct.c_int)]
 
 
 class agf2_fock_info(ct.Structure):

@@ -477,6 +477,21 @@ struct Shift {
   bool last_is_best;  // the extended-Hamiltonian buffers hold the decomposition at delta
 };
 
+// dn/d(delta) at fixed aufbau count k from one decomposition:
+// 4 sum_{x<k<=y} (C_x . C_y)^2 / (e_y - e_x), C = physical rows of the eigenvectors.
+double count_derivative(agf2_context* ctx, const Eig& eg, int k, int nmo, double* red) {
+  const int n = eg.n, nv = n - k;
+  double* S = ws(ctx, "sh_S", (size_t)k * nv);
+  DGemm g;  // S[x][y] = sum_p V[x n + p] V[(k + y) n + p]
+  g.M = k; g.N = nv; g.K = nmo;
+  g.A = eg.V; g.sAm = n; g.sAk = 1;
+  g.B = eg.V + (long long)k * n; g.sBk = 1; g.sBn = n;
+  g.C = S; g.sCm = nv; g.sCn = 1;
+  CK(dgemm(g, ctx->stream));
+  CK(shift_derivative(S, eg.w, k, nv, red + 512, red, ctx->stream));
+  return scalar(ctx, red + 512);
+}
+
 // Common shift of the auxiliary energies so that n(delta; k) = nelec, with k
 // the aufbau count at delta = 0.  n is increasing in delta with
 //   dn/d(delta) = 4 sum_{x<k<=y} (C_x . C_y)^2 / (e_y - e_x)
@@ -497,16 +512,7 @@ Shift solve_shift(agf2_context* ctx, const double* F, const double* E, const dou
       std::vector<double> ev = to_host(ctx, eg.w, n);
       k = aufbau(ev, wt, nelec).k;
     }
-    const int nv = n - k;
-    double* S = ws(ctx, "sh_S", (size_t)k * nv);
-    DGemm g;  // S[x][y] = sum_p V[x n + p] V[(k + y) n + p]
-    g.M = k; g.N = nv; g.K = nmo;
-    g.A = eg.V; g.sAm = n; g.sAk = 1;
-    g.B = eg.V + (long long)k * n; g.sBk = 1; g.sBn = n;
-    g.C = S; g.sCm = nv; g.sCn = 1;
-    CK(dgemm(g, ctx->stream));
-    CK(shift_derivative(S, eg.w, k, nv, red + 512, red, ctx->stream));
-    fp = scalar(ctx, red + 512);
+    fp = count_derivative(ctx, eg, k, nmo, red);
     return nelec_fixed_k(wt, k) - nelec;
   };
   double fp = 0.0;
@@ -622,17 +628,36 @@ FockOut fock_loop_impl(agf2_context* ctx, const double* h, const double* L, int 
   for (int cyc = 1; cyc <= o.max_cycle; ++cyc) {
     out.cycles = cyc;
     auto tc0 = std::chrono::steady_clock::now();
-    Shift sh = solve_shift(ctx, Fin, E, v, nmo, nse, nelec, o.shift_tol);
+    Shift sh{0.0, 0.0, 0, true, false};
+    double joint_step = 0.0;
+    Eig eg;
+    if (o.shift_mode == 1) {
+      // one decomposition per cycle; delta follows by one safeguarded Newton step
+      eg = diag_extended(ctx, Fin, E, v, 0.0, nmo, nse);
+      sh.evals = 1;
+    } else {
+      sh = solve_shift(ctx, Fin, E, v, nmo, nse, nelec, o.shift_tol);
+      CK(add_scalar(E, sh.delta, nse, s));
+      // the shift solve's last decomposition is the one at the chosen delta
+      eg = sh.last_is_best ? Eig{ws(ctx, "ext_H", (size_t)n * n), ws(ctx, "ext_w", n), n}
+                           : diag_extended(ctx, Fin, E, v, 0.0, nmo, nse);
+    }
     const double t_shift = seconds_since(tc0);
     out.evals += sh.evals;
-    out.nerr = sh.nerr;
-    CK(add_scalar(E, sh.delta, nse, s));
-    // the shift solve's last decomposition is the one at the chosen delta
-    Eig eg = sh.last_is_best ? Eig{ws(ctx, "ext_H", (size_t)n * n), ws(ctx, "ext_w", n), n}
-                             : diag_extended(ctx, Fin, E, v, 0.0, nmo, nse);
     std::vector<double> wt = pole_weights(ctx, eg, nmo);
     std::vector<double> ev = to_host(ctx, eg.w, n);
     Aufbau ab = aufbau(ev, wt, nelec);
+    if (o.shift_mode == 1) {
+      sh.nerr = ab.n - nelec;
+      if (std::fabs(sh.nerr) >= o.shift_tol) {
+        const double fp = count_derivative(ctx, eg, ab.k, nmo, red);
+        const double lim = 4.0;
+        joint_step = (fp > 0.0 && std::isfinite(fp)) ? -sh.nerr / fp : 0.0;
+        joint_step = std::max(-lim, std::min(lim, joint_step));
+      }
+      sh.delta = joint_step;
+    }
+    out.nerr = sh.nerr;
     out.k = ab.k;
     out.mu = ab.mu;
     CK(physical_block(eg.V, n, nmo, n, Cphys, s));  // Cphys[p][x]
@@ -661,10 +686,11 @@ FockOut fock_loop_impl(agf2_context* ctx, const double* h, const double* L, int 
                    cyc, sh.evals, 1e3 * t_shift, sh.delta, sh.nerr, ab.k, dD,
                    1e3 * seconds_since(tf0), 1e3 * seconds_since(tc0));
     CK(cudaMemcpyAsync(D, Dn, nn * sizeof(double), cudaMemcpyDeviceToDevice, s));
-    if (dD < o.tol_D) {
+    if (dD < o.tol_D && std::fabs(out.nerr) < o.shift_tol) {
       out.converged = 1;
       break;
     }
+    if (joint_step != 0.0) CK(add_scalar(E, joint_step, nse, s));
     if (cyc >= o.diis_start && space > 1) {
       // new entry (F_in, F_out - F_in) into the ring
       const int slot = (nh < space) ? nh : head;
@@ -706,6 +732,7 @@ agf2_fock_opts fock_defaults() {
   o.damping = 0.3;
   o.diis_start = 10;
   o.diis_space = 6;
+  o.shift_mode = 1;
   return o;
 }
 

@@ -119,9 +119,10 @@ def _first_iteration_self_energy(s, h):
     return np.concatenate([Eh, Ep]), np.concatenate([vh, vp], 1)
 
 
-def test_fock_loop_vs_oracle(cuda_handle, agf2_lib):
+@pytest.mark.parametrize("shift_mode", [0, 1])
+def test_fock_loop_vs_oracle(cuda_handle, agf2_lib, shift_mode):
     """Same synthetic self-energy (drawn by the seeded generator) into both
-    Fock loops."""
+    Fock loops; both shift modes reach the oracle's fixed point."""
     s = make_system(16, 4, 40, 5)
     h = O.hcore_from_mo_energies(s.eps, s.L, s.nocc)
     rng = np.random.default_rng(77)
@@ -132,9 +133,12 @@ def test_fock_loop_vs_oracle(cuda_handle, agf2_lib):
     ref = O.fock_loop(h, s.L, s.nelec, E, v, D0)
     hd, Ld, Ed, vd, Dd = dev(h), dev(s.L), dev(E), dev(v), dev(D0)
     F, eq, Cq = empty(16, 16), empty(16 + nse), empty(16, 16 + nse)
+    opts = agf2_lib.agf2_fock_opts_default()
+    opts.shift_mode = shift_mode
+    opts.max_cycle = 300
     rc, info = agf2_lib.agf2_fock_loop(cuda_handle.h, hd.data_ptr(), Ld.data_ptr(), s.naux, 16,
                                        s.nelec, Ed.data_ptr(), vd.data_ptr(), nse, Dd.data_ptr(),
-                                       F.data_ptr(), eq.data_ptr(), Cq.data_ptr())
+                                       F.data_ptr(), eq.data_ptr(), Cq.data_ptr(), opts)
     assert ref.converged and info.converged
     assert info.nocc_qmo == ref.nocc_qmo
     assert abs(info.mu - ref.mu) < 1e-9
