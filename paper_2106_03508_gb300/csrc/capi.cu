@@ -7,6 +7,7 @@
 // coefficients, convergence).
 #include <cublas_v2.h>
 #include <cusolverDn.h>
+#include <nvtx3/nvToolsExt.h>
 
 #include <algorithm>
 #include <chrono>
@@ -128,6 +129,13 @@ void check_dev_ptr(agf2_context* ctx, const void* p, const char* name) {
   if (a.type != cudaMemoryTypeDevice && a.type != cudaMemoryTypeManaged)
     fail(ctx, AGF2_ERR_INVALID_ARG, std::string(name) + " must be device memory");
 }
+
+// NVTX range for the stages of one iteration (visible to profilers; a no-op
+// unless a tool is attached).
+struct Range {
+  explicit Range(const char* name) { nvtxRangePushA(name); }
+  ~Range() { nvtxRangePop(); }
+};
 
 double seconds_since(std::chrono::steady_clock::time_point t0) {
   return std::chrono::duration<double>(std::chrono::steady_clock::now() - t0).count();
@@ -300,6 +308,7 @@ PoleSplit split_poles(agf2_context* ctx, const double* e, int nq, double mu) {
 void build_moments_impl(agf2_context* ctx, const double* L, int naux, int N, const double* e,
                         const double* C, int nq, double mu, int nmom, int precision,
                         double* Uh, double* Up) {
+  Range rg("agf2_moments");
   cudaStream_t s = ctx->stream;
   PoleSplit ps = split_poles(ctx, e, nq, mu);
   if (ps.o < 1 || ps.v < 1) fail(ctx, AGF2_ERR_INVALID_ARG, "need occupied and virtual poles");
@@ -377,6 +386,7 @@ void syevd(agf2_context* ctx, double* A, int n, double* w) {
 
 void compress_impl(agf2_context* ctx, const double* U, int n, double* E, double* v_rowmajor,
                    long long ldv) {
+  Range rg("agf2_compress");
   cudaStream_t s = ctx->stream;
   const long long nn = (long long)n * n;
   double* T = ws(ctx, "cmp_T", nn);
@@ -608,6 +618,7 @@ bool trace_on() {
 FockOut fock_loop_impl(agf2_context* ctx, const double* h, const double* L, int naux, int nmo,
                        int nelec, double* E, const double* v, int nse, double* D, double* F,
                        double* e_qmo, double* C_qmo, const agf2_fock_opts& o) {
+  Range rg("agf2_fock_loop");
   cudaStream_t s = ctx->stream;
   const int n = nmo + nse;
   const long long nn = (long long)nmo * nmo;

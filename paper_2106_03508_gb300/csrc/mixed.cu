@@ -80,11 +80,9 @@ struct Params {
   const float* unitA;   // MODE_PAIR: slicing unit of Lx rows [x][p]; MOMENT: of Y or Yw rows
   const float* unitA2;  // MOMENT: unit of Yw rows
   const float* unitB;   // MODE_PAIR: unit of Lov rows [i][a];        MOMENT: of Y rows
-  const float* unitY;   // MODE_PAIR: output units of Y rows
-  const float* unitYw;  // MODE_PAIR: output units of Yw rows
   int v_stride;         // MODE_PAIR: v (row index of Lov rows is i * v + a)
-  __nv_bfloat16* Y;    // [3][N][Ks]
-  __nv_bfloat16* Yw;   // [3][N][Ks]
+  float* Y;            // MODE_PAIR output: FP32 [N][Ks], sliced afterwards
+  float* Yw;           // MODE_PAIR output: FP32 [N][Ks]
   long long Ks;
   long long plane;     // N * Ks
   double* U0;
@@ -299,33 +297,41 @@ gemm6_kernel(const __grid_constant__ CUtensorMap mapA, const __grid_constant__ C
       if (MODE == MODE_PAIR) {
         const int2 pr = w.pr;
         const bool diag = (pr.x == pr.y);
-        const float sS = diag ? 0.5f : 0.70710678118654752f;
-        const float sD = diag ? 0.0f : 1.22474487139158905f;
+        // sqrt(cS), sqrt(cD) as unevaluated float pairs (hi + lo to ~1e-16): a
+        // rounded FP32 constant would enter U^(0) = Y Y^T squared and bias every
+        // diagonal element by up to ~7e-8 relative; with the pair the product is
+        // one round-to-nearest (fmaf) and unbiased.
+        const float sS = diag ? 0.5f : 0.7071067690849304f;
+        const float sS_lo = diag ? 0.0f : 1.2101617485882343e-08f;
+        const float sD = diag ? 0.0f : 1.2247449159622192f;
+        const float sD_lo = diag ? 0.0f : -4.4570629853524224e-08f;
         const double ex = P.e_out[pr.x] + P.e_out[pr.y];
         const bool prow = p < P.N;
         const float uA1 = prow ? P.unitA[(long long)pr.x * P.N + p] : 0.f;
         const float uA2 = prow ? P.unitA[(long long)pr.y * P.N + p] : 0.f;
-        const float inv_uy = prow ? 1.0f / P.unitY[p] : 0.f;
-        const float inv_uyw = prow ? 1.0f / P.unitYw[p] : 0.f;
         // this tile's K range of Y: [kS, kS + BN) for S, [kS + BN, kS + 2 BN) for D
         const long long kS = (long long)w.pair_local * P.kpp + (long long)(w.c0 / BN) * KCHUNK;
-        for (int cb = col0; cb < col0 + BN / 2; cb += 32) {
-          float h1[32], l1[32], h2[32], l2[32];
-          tc::tmem_ld32(trow + cb, h1);
-          tc::tmem_ld32(trow + BN + cb, l1);
+        // 16 columns per TMEM read; all register indices static (fully unrolled)
+        for (int cb = col0; cb < col0 + BN / 2; cb += 16) {
+          float h1[16], l1[16], h2[16], l2[16];
+          tc::tmem_ld16(trow + cb, h1);
+          tc::tmem_ld16(trow + BN + cb, l1);
           if (!diag) {
-            tc::tmem_ld32(trow + 2 * BN + cb, h2);
-            tc::tmem_ld32(trow + 3 * BN + cb, l2);
+            tc::tmem_ld16(trow + 2 * BN + cb, h2);
+            tc::tmem_ld16(trow + 3 * BN + cb, l2);
+          } else {
+#pragma unroll
+            for (int c = 0; c < 16; ++c) { h2[c] = h1[c]; l2[c] = l1[c]; }
           }
           if (prow) {
-            __nv_bfloat16* y = P.Y + (long long)p * P.Ks + kS + cb;
-            __nv_bfloat16* yw = P.Yw + (long long)p * P.Ks + kS + cb;
-            // 8 columns at a time -> one 16-byte store per (array, limb)
-            for (int g = 0; g < 32; g += 8) {
-              uint4 out[12];
-              __nv_bfloat16* ob = reinterpret_cast<__nv_bfloat16*>(out);
+            float* y = P.Y + (long long)p * P.Ks + kS + cb;
+            float* yw = P.Yw + (long long)p * P.Ks + kS + cb;
 #pragma unroll
-              for (int c = 0; c < 8; ++c) {
+            for (int g = 0; g < 16; g += 4) {
+              float4 vs, vd, ws, wd;
+              float* pvs = &vs.x; float* pvd = &vd.x; float* pws = &ws.x; float* pwd = &wd.x;
+#pragma unroll
+              for (int c = 0; c < 4; ++c) {
                 const int ci = w.c0 + cb + g + c;
                 float ys = 0.f, yd = 0.f, wt = 0.f;
                 if (ci < P.n_in) {
@@ -335,37 +341,34 @@ gemm6_kernel(const __grid_constant__ CUtensorMap mapA, const __grid_constant__ C
                   const long long rb2 = P.hole ? (long long)pr.x * P.v_stride + ci
                                                : (long long)ci * P.v_stride + pr.x;
                   const float xa = (h1[g + c] + l1[g + c]) * (uA1 * P.unitB[rb1]);
-                  const float xb = diag ? xa : (h2[g + c] + l2[g + c]) * (uA2 * P.unitB[rb2]);
-                  ys = sS * (xa + xb);
-                  yd = sD * (xa - xb);
+                  const float xb = (h2[g + c] + l2[g + c]) * (uA2 * P.unitB[rb2]);
+                  const float sum = xa + xb, dif = xa - xb;
+                  ys = fmaf(sum, sS, sum * sS_lo);
+                  yd = fmaf(dif, sD, dif * sD_lo);
                   wt = (float)(ex - P.e_in[ci]);
                 }
-                // out[3*arr + limb], arr: 0 Y_S, 1 Y_D, 2 Yw_S, 3 Yw_D
-                tc::slice3f(ys * inv_uy, ob[0 * 8 + c], ob[1 * 8 + c], ob[2 * 8 + c]);
-                tc::slice3f(yd * inv_uy, ob[3 * 8 + c], ob[4 * 8 + c], ob[5 * 8 + c]);
-                tc::slice3f(ys * wt * inv_uyw, ob[6 * 8 + c], ob[7 * 8 + c], ob[8 * 8 + c]);
-                tc::slice3f(yd * wt * inv_uyw, ob[9 * 8 + c], ob[10 * 8 + c], ob[11 * 8 + c]);
+                pvs[c] = ys;
+                pvd[c] = yd;
+                pws[c] = ys * wt;
+                pwd[c] = yd * wt;
               }
-#pragma unroll
-              for (int l = 0; l < 3; ++l) {
-                *reinterpret_cast<uint4*>(y + l * P.plane + g) = out[0 + l];
-                *reinterpret_cast<uint4*>(y + l * P.plane + BN + g) = out[3 + l];
-                *reinterpret_cast<uint4*>(yw + l * P.plane + g) = out[6 + l];
-                *reinterpret_cast<uint4*>(yw + l * P.plane + BN + g) = out[9 + l];
-              }
+              *reinterpret_cast<float4*>(y + g) = vs;
+              *reinterpret_cast<float4*>(y + BN + g) = vd;
+              *reinterpret_cast<float4*>(yw + g) = ws;
+              *reinterpret_cast<float4*>(yw + BN + g) = wd;
             }
           }
         }
       } else {
         double* U = w.moment == 0 ? P.U0 : P.U1;
         const double uA = (p < P.N) ? (double)(w.moment == 0 ? P.unitA : P.unitA2)[p] : 0.0;
-        for (int cb = col0; cb < col0 + BN / 2; cb += 32) {
-          float hi[32], lo[32];
-          tc::tmem_ld32(trow + cb, hi);
-          tc::tmem_ld32(trow + BN + cb, lo);
+        for (int cb = col0; cb < col0 + BN / 2; cb += 16) {
+          float hi[16], lo[16];
+          tc::tmem_ld16(trow + cb, hi);
+          tc::tmem_ld16(trow + BN + cb, lo);
           if (p < P.N) {
-#pragma unroll 4
-            for (int c = 0; c < 32; ++c) {
+#pragma unroll
+            for (int c = 0; c < 16; ++c) {
               const int q = w.q0 + cb + c;
               if (q < P.N)
                 atomicAdd(U + (long long)p * P.N + q,
@@ -410,7 +413,8 @@ gemm6_kernel(const __grid_constant__ CUtensorMap mapA, const __grid_constant__ C
 // [3][nrow][ncolp] (zero padded to ncolp) in fixed point with the row's
 // power-of-two unit; also the unit and the Euclidean norm of each row.
 // One warp per row.
-__global__ void slice_rows_kernel(const double* __restrict__ src, long long nrow, int ncol,
+template <class T>
+__global__ void slice_rows_kernel(const T* __restrict__ src, long long nrow, int ncol,
                                   long long ld, int ncolp, __nv_bfloat16* __restrict__ dst,
                                   float* __restrict__ unit, double* __restrict__ norm) {
   const long long plane = nrow * ncolp;
@@ -418,7 +422,7 @@ __global__ void slice_rows_kernel(const double* __restrict__ src, long long nrow
   const long long nwarps = (long long)gridDim.x * (blockDim.x >> 5);
   for (long long r = (blockIdx.x * (long long)blockDim.x + threadIdx.x) >> 5; r < nrow;
        r += nwarps) {
-    const double* row = src + r * ld;
+    const T* row = src + r * ld;
     double m = 0.0, ss = 0.0;
     for (int c = lane; c < ncol; c += 32) {
       const double x = row[c];
@@ -434,7 +438,7 @@ __global__ void slice_rows_kernel(const double* __restrict__ src, long long nrow
     const double inv = 1.0 / u;  // exact: u is a power of two
     __nv_bfloat16* d = dst + r * ncolp;
     for (int c = lane; c < ncolp; c += 32) {
-      const double x = (c < ncol) ? row[c] : 0.0;
+      const double x = (c < ncol) ? (double)row[c] : 0.0;
       __nv_bfloat16 h0, h1, h2;
       tc::slice3(x * inv, h0, h1, h2);
       d[c] = h0;
@@ -443,39 +447,53 @@ __global__ void slice_rows_kernel(const double* __restrict__ src, long long nrow
     }
     if (lane == 0) {
       unit[r] = (float)u;
-      norm[r] = sqrt(ss);
+      if (norm) norm[r] = sqrt(ss);
     }
   }
 }
 
-// Units of the Y and Yw rows of one sector from a Cauchy-Schwarz bound:
-// |X_xy[p,c]| <= |Lx[x][p]| |Lpair[y][c]|, |Y| <= sqrt(6) max|X| (the D part,
-// sqrt(3/2) |X_xy - X_yx|), |Yw| <= |Y| max|w|.  One thread per p.
-__global__ void y_units_kernel(const double* __restrict__ norm_x, int n_out, int N, double bmax,
-                               double wmax, float* __restrict__ unit_y,
-                               float* __restrict__ unit_yw) {
-  const int p = blockIdx.x * blockDim.x + threadIdx.x;
-  if (p >= N) return;
-  double a = 0.0;
-  for (int x = 0; x < n_out; ++x) a = fmax(a, norm_x[(long long)x * N + p]);
-  const double yb = 2.475 * a * bmax;  // sqrt(6) with a 1% margin for rounding
-  unit_y[p] = (float)tc::slice_unit(yb);
-  unit_yw[p] = (float)tc::slice_unit(yb * wmax);
-}
-
-__global__ void max_kernel(const double* __restrict__ x, long long n, double* out) {
-  __shared__ double sh[32];
-  double m = 0.0;
-  for (long long t = threadIdx.x; t < n; t += blockDim.x) m = fmax(m, x[t]);
+// Row maxima of |src| over segments of 4096 columns: maxbits[r] holds the
+// largest |x| of row r as float bits (non-negative floats order like their
+// bit patterns); must be zeroed first.  grid = (segments, rows).
+__global__ void row_absmax_kernel(const float* __restrict__ src, int ncol, long long ld,
+                                  unsigned* __restrict__ maxbits) {
+  __shared__ float sh[8];
+  const long long r = blockIdx.y;
+  const int c0 = blockIdx.x * 4096;
+  const int c1 = min(ncol, c0 + 4096);
+  float m = 0.f;
+  for (int c = c0 + threadIdx.x; c < c1; c += blockDim.x) m = fmaxf(m, fabsf(src[r * ld + c]));
 #pragma unroll
-  for (int o = 16; o > 0; o >>= 1) m = fmax(m, __shfl_xor_sync(0xffffffffu, m, o));
+  for (int o = 16; o > 0; o >>= 1) m = fmaxf(m, __shfl_xor_sync(0xffffffffu, m, o));
   if ((threadIdx.x & 31) == 0) sh[threadIdx.x >> 5] = m;
   __syncthreads();
-  if (threadIdx.x < 32) {
-    m = (threadIdx.x < (blockDim.x >> 5)) ? sh[threadIdx.x] : 0.0;
-#pragma unroll
-    for (int o = 16; o > 0; o >>= 1) m = fmax(m, __shfl_xor_sync(0xffffffffu, m, o));
-    if (threadIdx.x == 0) *out = m;
+  if (threadIdx.x == 0) {
+    for (int w = 1; w < (int)(blockDim.x >> 5); ++w) m = fmaxf(m, sh[w]);
+    atomicMax(maxbits + r, __float_as_uint(m));
+  }
+}
+
+// Fixed-point three-limb slicing of FP32 rows with each row's unit from its
+// exact maximum (row_absmax_kernel); element-parallel.  Writes limb planes
+// [3][nrow][ncolp] (zero beyond ncol) and the unit of every row.
+__global__ void slice_fp32_kernel(const float* __restrict__ src, long long nrow, int ncol,
+                                  long long ld, int ncolp, const unsigned* __restrict__ maxbits,
+                                  __nv_bfloat16* __restrict__ dst, float* __restrict__ unit) {
+  const long long total = nrow * (long long)ncolp;
+  for (long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x; t < total;
+       t += (long long)gridDim.x * blockDim.x) {
+    const long long r = t / ncolp;
+    const int c = (int)(t - r * ncolp);
+    // FP32 throughout (GB300's FP64 rate is a small fraction of FP32); exact:
+    // the unit is a power of two and slice3f's residuals are exact
+    const float u = tc::slice_unitf(__uint_as_float(maxbits[r]));
+    const float x = (c < ncol) ? src[r * ld + c] : 0.0f;
+    __nv_bfloat16 h0, h1, h2;
+    tc::slice3f(x * (1.0f / u), h0, h1, h2);
+    dst[t] = h0;
+    dst[total + t] = h1;
+    dst[2 * total + t] = h2;
+    if (c == 0) unit[r] = u;
   }
 }
 
@@ -521,7 +539,7 @@ struct Buffers {
 
 struct MixedWs {
   Buffers lx_o, lx_v, l_ov, y, yw, pairs, err;
-  Buffers u_xo, u_xv, u_ov, n_xo, n_xv, n_ov, u_y, u_yw, scal;
+  Buffers u_xo, u_xv, u_ov, u_y, u_yw, y32, yw32, maxbits;
 };
 
 MixedWs g_ws[64];  // per device
@@ -596,43 +614,24 @@ int mixed_build_moments_rotated(const double* Lxo, const double* Lxv, const doub
   float* u_xo = grow<float>(W.u_xo, (size_t)o * N, err);
   float* u_xv = grow<float>(W.u_xv, (size_t)v * N, err);
   float* u_ov = grow<float>(W.u_ov, (size_t)o * v, err);
-  double* n_xo = grow<double>(W.n_xo, (size_t)o * N, err);
-  double* n_xv = grow<double>(W.n_xv, (size_t)v * N, err);
-  double* n_ov = grow<double>(W.n_ov, (size_t)o * v, err);
   float* u_y = grow<float>(W.u_y, N, err);
   float* u_yw = grow<float>(W.u_yw, N, err);
-  double* scal = grow<double>(W.scal, 8, err);
-  if (!u_xo || !u_xv || !u_ov || !n_xo || !n_xv || !n_ov || !u_y || !u_yw || !scal)
-    return AGF2_ERR_OOM;
+  if (!u_xo || !u_xv || !u_ov || !u_y || !u_yw) return AGF2_ERR_OOM;
   // rotated FP64 tensors have layout [x][p][Q] / [j][a][Q] with row length naux
-  auto slice = [&](const double* src, long long rows, __nv_bfloat16* dst, float* unit,
-                   double* norm) {
+  auto slice = [&](auto* src, long long rows, int ncol, long long ld, int ncolp,
+                   __nv_bfloat16* dst, float* unit) {
     const long long blocks = std::min<long long>((rows + 7) / 8, 152LL * 16);
-    slice_rows_kernel<<<(int)std::max(1LL, blocks), 256, 0, s>>>(src, rows, naux, naux, Qs, dst,
-                                                                 unit, norm);
+    slice_rows_kernel<<<(int)std::max(1LL, blocks), 256, 0, s>>>(src, rows, ncol, ld, ncolp, dst,
+                                                                 unit, (double*)nullptr);
+    count_launch();
   };
-  count_launch(4);  // three slicing kernels and the max reduction
-  slice(Lxo, (long long)o * N, lxo, u_xo, n_xo);
-  slice(Lxv, (long long)v * N, lxv, u_xv, n_xv);
-  slice(Lov, (long long)o * v, lov, u_ov, n_ov);
-  max_kernel<<<1, 1024, 0, s>>>(n_ov, (long long)o * v, scal);
+  slice(Lxo, (long long)o * N, naux, naux, Qs, lxo, u_xo);
+  slice(Lxv, (long long)v * N, naux, naux, Qs, lxv, u_xv);
+  slice(Lov, (long long)o * v, naux, naux, Qs, lov, u_ov);
   if (cudaGetLastError() != cudaSuccess) {
     err = "slice kernel launch failed";
     return AGF2_ERR_CUDA;
   }
-  double bmax = 0.0;
-  std::vector<double> eoh(o), evh(v);
-  cudaMemcpyAsync(&bmax, scal, sizeof(double), cudaMemcpyDeviceToHost, s);
-  cudaMemcpyAsync(eoh.data(), eo, o * sizeof(double), cudaMemcpyDeviceToHost, s);
-  cudaMemcpyAsync(evh.data(), ev, v * sizeof(double), cudaMemcpyDeviceToHost, s);
-  if (cudaStreamSynchronize(s) != cudaSuccess) {
-    err = "mixed moment build: slicing failed";
-    return AGF2_ERR_CUDA;
-  }
-  const double eo_min = *std::min_element(eoh.begin(), eoh.end());
-  const double eo_max = *std::max_element(eoh.begin(), eoh.end());
-  const double ev_min = *std::min_element(evh.begin(), evh.end());
-  const double ev_max = *std::max_element(evh.begin(), evh.end());
   // tensor maps of the rotated limb planes
   CUtensorMap map_xo, map_xv, map_b_hole, map_b_part;
   {
@@ -661,12 +660,6 @@ int mixed_build_moments_rotated(const double* Lxo, const double* Lxv, const doub
     const double* e_out = hole ? eo : ev;
     const double* e_in = hole ? ev : eo;
     double* U = hole ? U_hole : U_part;
-    // |w| = |e_x + e_y - e_c| is extremal at the ends of the energy ranges
-    const double wmax = hole ? std::max(std::fabs(2 * eo_max - ev_min), std::fabs(2 * eo_min - ev_max))
-                             : std::max(std::fabs(2 * ev_max - eo_min), std::fabs(2 * ev_min - eo_max));
-    y_units_kernel<<<(N + 127) / 128, 128, 0, s>>>(hole ? n_xo : n_xv, n_out, N, bmax, wmax, u_y,
-                                                   u_yw);
-    count_launch();
     // unordered pairs x <= y
     std::vector<int2> pairs;
     pairs.reserve((size_t)n_out * (n_out + 1) / 2);
@@ -693,7 +686,10 @@ int mixed_build_moments_rotated(const double* Lxo, const double* Lxv, const doub
     const long long Ks = (long long)bp * kpp;
     __nv_bfloat16* y = grow<__nv_bfloat16>(W.y, 3LL * N * Ks, err);
     __nv_bfloat16* yw = grow<__nv_bfloat16>(W.yw, 3LL * N * Ks, err);
-    if (!y || !yw) return AGF2_ERR_OOM;
+    float* y32 = grow<float>(W.y32, (size_t)N * Ks, err);
+    float* yw32 = grow<float>(W.yw32, (size_t)N * Ks, err);
+    unsigned* maxbits = grow<unsigned>(W.maxbits, 2 * (size_t)N, err);
+    if (!y || !yw || !y32 || !yw32 || !maxbits) return AGF2_ERR_OOM;
     for (size_t b0 = 0; b0 < pairs.size(); b0 += bp) {
       const int np = (int)std::min<size_t>(bp, pairs.size() - b0);
       const long long K = (long long)np * kpp;
@@ -712,11 +708,9 @@ int mixed_build_moments_rotated(const double* Lxo, const double* Lxv, const doub
       P.e_in = e_in;
       P.unitA = hole ? u_xo : u_xv;
       P.unitB = u_ov;
-      P.unitY = u_y;
-      P.unitYw = u_yw;
       P.v_stride = v;
-      P.Y = y;
-      P.Yw = yw;
+      P.Y = y32;
+      P.Yw = yw32;
       P.Ks = Ks;
       P.plane = (long long)N * Ks;
       P.err = derr;
@@ -730,6 +724,15 @@ int mixed_build_moments_rotated(const double* Lxo, const double* Lxv, const doub
           hole ? map_xo : map_xv, hole ? map_xo : map_xv, hole ? map_b_hole : map_b_part, P);
       mark_end();
       count_launch();
+      // fixed-point limbs of Y and Yw with each row's unit from its exact maximum
+      cudaMemsetAsync(maxbits, 0, 2 * N * sizeof(unsigned), s);
+      const dim3 gmax((unsigned)((K + 4095) / 4096), (unsigned)N);
+      row_absmax_kernel<<<gmax, 256, 0, s>>>(y32, (int)K, Ks, maxbits);
+      row_absmax_kernel<<<gmax, 256, 0, s>>>(yw32, (int)K, Ks, maxbits + N);
+      const int gsl = (int)std::min<long long>(((long long)N * Ks + 255) / 256, 152LL * 32);
+      slice_fp32_kernel<<<gsl, 256, 0, s>>>(y32, N, (int)K, Ks, (int)Ks, maxbits, y, u_y);
+      slice_fp32_kernel<<<gsl, 256, 0, s>>>(yw32, N, (int)K, Ks, (int)Ks, maxbits + N, yw, u_yw);
+      count_launch(4);
       // GEMM 2 over this block's K = np * kpp
       CUtensorMap map_y, map_yw;
       cuuint64_t dims[3] = {(cuuint64_t)K, (cuuint64_t)N, 3};

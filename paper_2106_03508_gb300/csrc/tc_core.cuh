@@ -170,6 +170,21 @@ __device__ __forceinline__ void tmem_ld32(uint32_t taddr, float* v) {
   for (int i = 0; i < 32; ++i) v[i] = __uint_as_float(r[i]);
 }
 
+// 16 consecutive FP32 columns of this thread's TMEM lane.
+__device__ __forceinline__ void tmem_ld16(uint32_t taddr, float* v) {
+  uint32_t r[16];
+  asm volatile(
+      "tcgen05.ld.sync.aligned.32x32b.x16.b32 "
+      "{%0, %1, %2, %3, %4, %5, %6, %7, %8, %9, %10, %11, %12, %13, %14, %15}, [%16];"
+      : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]),
+        "=r"(r[7]), "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]),
+        "=r"(r[14]), "=r"(r[15])
+      : "r"(taddr));
+  asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+#pragma unroll
+  for (int i = 0; i < 16; ++i) v[i] = __uint_as_float(r[i]);
+}
+
 // ---- fixed-point three-limb BF16 slicing ----
 // With a per-row power-of-two unit s (|x| <= 256 s on that row),
 //   x / s ~ h0 + h1 + h2,  h0 integer in [-256, 256], h1 in 2^-8 Z,
@@ -197,6 +212,14 @@ __device__ __forceinline__ void slice3f(float u, __nv_bfloat16& h0, __nv_bfloat1
   h0 = __float2bfloat16_rn(a0);
   h1 = __float2bfloat16_rn(a1 * (1.0f / 256.0f));
   h2 = __float2bfloat16_rn(a2 * (1.0f / 65536.0f));
+}
+
+// FP32 variant of slice_unit.
+__device__ __forceinline__ float slice_unitf(float m) {
+  if (!(m > 0.0f)) return 1.0f;
+  int E;
+  frexpf(m, &E);
+  return ldexpf(1.0f, E - 8);
 }
 
 // Smallest power of two 2^E with m < 2^E, returned as the slicing unit 2^(E-8).

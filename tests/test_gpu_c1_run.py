@@ -57,8 +57,7 @@ def test_c1_mixed_vs_fp64_errors(cuda_handle, agf2_lib):
                                                            x["ip"] - y["ip"], x["ea"] - y["ea"]))
     err = {k: max(abs(x[k] - y[k]) for x, y in zip(a, b)) for k in ("E_tot", "ip", "ea")}
     print("c1 mixed vs FP64 oracle max |error| over", NIT, "iterations:", err)
-    # first iteration (moments from the HF reference): the per-iteration error
-    assert abs(a[0]["ip"] - b[0]["ip"]) < 1e-5 and abs(a[0]["ea"] - b[0]["ea"]) < 1e-5
-    assert abs(a[0]["E_tot"] - b[0]["E_tot"]) < 1e-5
-    # whole trajectory (errors carried through the self-consistency)
-    assert err["ip"] < 5e-5 and err["ea"] < 5e-5 and err["E_tot"] < 1e-4
+    # targets of the split-precision path: IP/EA within 1e-5 Ha, E_tot within
+    # 1e-6 Ha, over the whole self-consistent trajectory
+    assert err["ip"] < 1e-5 and err["ea"] < 1e-5
+    assert err["E_tot"] < 1e-6
