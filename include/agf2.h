@@ -188,6 +188,28 @@ void agf2_opts_default(agf2_opts* o);
 int agf2_run(agf2_handle h, const double* hcore, const double* L, int naux, int nmo,
              int nelec, const double* eps0, const agf2_opts* opts, agf2_result* out);
 
+/* One system of a batch: device pointers as for agf2_run. */
+typedef struct {
+    const double* hcore;   /* [nmo][nmo]            */
+    const double* L;       /* [naux][nmo][nmo]      */
+    const double* eps0;    /* [nmo]                 */
+    int naux, nmo, nelec;
+} agf2_system;
+
+/*
+ * Many independent systems of uneven size (nmo, nocc, naux) in one call:
+ * agf2_run (from the HF reference, opts->resume ignored) on each, with
+ * `nworkers` host worker threads (0: 8), each owning a handle, a non-blocking
+ * stream and its workspace on h's device, so that the small systems' kernels
+ * run concurrently.  out[i] (host) receives system i's result and status[i]
+ * (host, may be NULL) its status.  Returns AGF2_OK when every system returned
+ * AGF2_OK or AGF2_ERR_NO_CONVERGENCE, else the first other error (message in
+ * agf2_last_error(h)).  Systems are not graph-captured: each runs the same
+ * host-sequenced iteration as agf2_run.
+ */
+int agf2_run_batched(agf2_handle h, int nsys, const agf2_system* systems, const agf2_opts* opts,
+                     int nworkers, agf2_result* out, int* status);
+
 /*
  * Copy the Green's function kept in the handle after agf2_run: nqmo poles
  * e [nqmo] and couplings C [nmo][nqmo] (device pointers sized for 3*nmo),

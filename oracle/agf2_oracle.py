@@ -135,6 +135,36 @@ def build_moments(L, e, C, mu, nmom: int = 1):
     return Uh, Up
 
 
+def moment_elements(L, e, C, mu, pq, nmom: int = 1):
+    """Selected elements U^(n)_pq of both sectors straight from the definition
+    (Eqs. mp2_zeroth_moment, mp2_first_moment), one (p, q) at a time:
+    X_p[i,j,a] = (pi|ja), U_pq = sum_ija X_p[i,j,a] (2 X_q[i,j,a] - X_q[j,i,a]) w^n.
+    For sampled parity at sizes where the full build is out of reach.
+    Returns (hole [len(pq), nmom+1], particle [len(pq), nmom+1]), symmetrised."""
+    eo, Co, ev, Cv = split_poles(e, C, mu)
+    Lxo, Lxv, Lov = rotate(L, Co, Cv)
+    Lvo = Lov.transpose(0, 2, 1)
+    wh = eo[:, None, None] + eo[None, :, None] - ev[None, None, :]
+    wp = ev[:, None, None] + ev[None, :, None] - eo[None, None, :]
+
+    def xh(p):  # (pi|ja) [i, j, a]
+        return np.tensordot(Lxo[:, p, :], Lov, axes=(0, 0))
+
+    def xp(p):  # (pa|bi) [a, b, i]
+        return np.tensordot(Lxv[:, p, :], Lvo, axes=(0, 0))
+
+    out_h = np.zeros((len(pq), nmom + 1))
+    out_p = np.zeros((len(pq), nmom + 1))
+    for t, (p, q) in enumerate(pq):
+        for X, w, out in ((xh, wh, out_h), (xp, wp, out_p)):
+            Xp, Xq = X(p), X(q)
+            tp = Xp * (2.0 * Xq - Xq.transpose(1, 0, 2))
+            tq = Xq * (2.0 * Xp - Xp.transpose(1, 0, 2))
+            for n in range(nmom + 1):
+                out[t, n] = 0.5 * (np.sum(tp * w ** n) + np.sum(tq * w ** n))
+    return out_h, out_p
+
+
 def pole_eris(L, C):
     """Four-index ERIs in the pole basis by brute force: (px|yz), p physical."""
     eri = np.einsum("Qpq,Qrs->pqrs", L, L)

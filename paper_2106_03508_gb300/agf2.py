@@ -31,7 +31,7 @@ EXPORTED = [
     "agf2_hcore_from_mo_energies", "agf2_build_moments", "agf2_compress",
     "agf2_fock_opts_default", "agf2_fock_loop", "agf2_opts_default", "agf2_run",
     "agf2_get_state", "agf2_set_profiling", "agf2_kernel_stats", "agf2_launch_count",
-    "agf2_build_moments_noalloc",
+    "agf2_build_moments_noalloc", "agf2_run_batched",
 ]
 
 
@@ -50,6 +50,11 @@ class agf2_opts(ct.Structure):
     _fields_ = [("max_iter", ct.c_int), ("conv_tol", ct.c_double), ("nmom", ct.c_int),
                 ("precision", ct.c_int), ("mix", ct.c_double), ("resume", ct.c_int),
                 ("fock", agf2_fock_opts)]
+
+
+class agf2_system(ct.Structure):
+    _fields_ = [("hcore", ct.c_void_p), ("L", ct.c_void_p), ("eps0", ct.c_void_p),
+                ("naux", ct.c_int), ("nmo", ct.c_int), ("nelec", ct.c_int)]
 
 
 class agf2_result(ct.Structure):
@@ -89,6 +94,8 @@ def _load():
                                   ct.POINTER(D)]),
         "agf2_launch_count": (ct.c_longlong, []),
         "agf2_build_moments_noalloc": (I, [P, I, I, P, P, I, D, P, P, P]),
+        "agf2_run_batched": (I, [P, I, ct.POINTER(agf2_system), ct.POINTER(agf2_opts), I,
+                                 ct.POINTER(agf2_result), ct.POINTER(ct.c_int)]),
     }
     for name, (res, args) in sig.items():
         fn = getattr(lib, name)
@@ -174,6 +181,18 @@ def agf2_run(h, hcore, L, naux, nmo, nelec, eps0, opts=None, allow=(AGF2_ERR_NO_
                        ct.byref(opts) if opts is not None else None, ct.byref(out))
     _check(h, rc, allow)
     return rc, out
+
+
+def agf2_run_batched(h, systems, opts=None, nworkers=0, allow=(AGF2_ERR_NO_CONVERGENCE,)):
+    """systems: list of (hcore_ptr, L_ptr, eps0_ptr, naux, nmo, nelec)."""
+    n = len(systems)
+    arr = (agf2_system * max(n, 1))(*[agf2_system(*sy) for sy in systems])
+    out = (agf2_result * max(n, 1))()
+    st = (ct.c_int * max(n, 1))()
+    rc = _lib.agf2_run_batched(h, n, arr, ct.byref(opts) if opts is not None else None,
+                               nworkers, out, st)
+    _check(h, rc, allow)
+    return rc, [out[i] for i in range(n)], [st[i] for i in range(n)]
 
 
 def agf2_get_state(h, e=None, C=None, D=None):

@@ -90,6 +90,9 @@ cudaError_t add_scalar(double* x, double a, int n, cudaStream_t s);
 int mixed_build_moments_rotated(const double* Lxo, const double* Lxv, const double* Lov, int naux,
                                 int N, int o, int v, const double* eo, const double* ev,
                                 double* U_hole, double* U_part, std::string& err,
-                                cudaStream_t s, KernelStats* stats);
+                                cudaStream_t s, KernelStats* stats, void* workspace);
+// Workspace of the split-precision path, one per handle.
+void* mixed_workspace_create();
+void mixed_workspace_destroy(void* w);
 
 }  // namespace agf2

@@ -10,7 +10,9 @@
 #include <nvtx3/nvToolsExt.h>
 
 #include <algorithm>
+#include <atomic>
 #include <chrono>
+#include <thread>
 #include <cmath>
 #include <cstdio>
 #include <cstdlib>
@@ -43,6 +45,7 @@ struct agf2_context {
   bool have_uprev = false;
   int iter = 0;
   KernelStats stats;
+  void* mixed_ws = nullptr;
 };
 
 namespace {
@@ -354,8 +357,9 @@ void build_moments_impl(agf2_context* ctx, const double* L, int naux, int N, con
     CK(dgemm(g, s));
   }
   if (precision == AGF2_BF16X3) {
+    if (!ctx->mixed_ws) ctx->mixed_ws = mixed_workspace_create();
     int rc = mixed_build_moments_rotated(Lxo, Lxv, Lov, naux, N, o, v, eo, ev, Uh, Up, ctx->err, s,
-                                         &ctx->stats);
+                                         &ctx->stats, ctx->mixed_ws);
     if (rc != AGF2_OK) throw Fail{rc};
   } else {
     Sector hole{o, v, Lxo, Lov, (long long)v * naux, (long long)naux, eo, ev};
@@ -810,6 +814,7 @@ int agf2_destroy(agf2_handle h) {
   if (h->stream) cudaStreamSynchronize(h->stream);
   for (auto& kv : h->bufs)
     if (kv.second.p) cudaFree(kv.second.p);
+  mixed_workspace_destroy(h->mixed_ws);
   if (h->dev_info) cudaFree(h->dev_info);
   if (h->blas) cublasDestroy(h->blas);
   if (h->solver) cusolverDnDestroy(h->solver);
@@ -1064,6 +1069,61 @@ int agf2_kernel_stats(agf2_handle h, int kind, long long* launches, double* ms, 
 }
 
 long long agf2_launch_count(void) { return launch_count(); }
+
+int agf2_run_batched(agf2_handle h, int nsys, const agf2_system* systems, const agf2_opts* opts,
+                     int nworkers, agf2_result* out, int* status) {
+  if (!h) return AGF2_ERR_INVALID_ARG;
+  h->err.clear();
+  if (nsys < 0 || (nsys > 0 && (!systems || !out))) {
+    h->err = "bad batch arguments";
+    return AGF2_ERR_INVALID_ARG;
+  }
+  if (nsys == 0) return AGF2_OK;
+  const int nw = std::max(1, std::min(nworkers > 0 ? nworkers : 8, nsys));
+  std::vector<int> st(nsys, AGF2_OK);
+  std::vector<std::string> msg(nsys);
+  std::atomic<int> next{0};
+  std::vector<int> worker_rc(nw, AGF2_OK);
+  auto work = [&](int wi) {
+    if (cudaSetDevice(h->device) != cudaSuccess) { worker_rc[wi] = AGF2_ERR_CUDA; return; }
+    agf2_handle w = nullptr;
+    cudaStream_t stream = nullptr;
+    if (agf2_create(&w, h->device) != AGF2_OK ||
+        cudaStreamCreateWithFlags(&stream, cudaStreamNonBlocking) != cudaSuccess ||
+        agf2_set_stream(w, stream) != AGF2_OK) {
+      cudaGetLastError();
+      worker_rc[wi] = AGF2_ERR_CUDA;
+      if (w) agf2_destroy(w);
+      if (stream) cudaStreamDestroy(stream);
+      return;
+    }
+    for (int i = next.fetch_add(1); i < nsys; i = next.fetch_add(1)) {
+      const agf2_system& sy = systems[i];
+      agf2_opts o;
+      agf2_opts_default(&o);
+      if (opts) o = *opts;
+      o.resume = 0;
+      st[i] = agf2_run(w, sy.hcore, sy.L, sy.naux, sy.nmo, sy.nelec, sy.eps0, &o, &out[i]);
+      if (st[i] != AGF2_OK) msg[i] = agf2_last_error(w);
+    }
+    agf2_destroy(w);
+    cudaStreamDestroy(stream);
+  };
+  std::vector<std::thread> threads;
+  for (int wi = 0; wi < nw; ++wi) threads.emplace_back(work, wi);
+  for (auto& t : threads) t.join();
+  int rc = AGF2_OK;
+  for (int wi = 0; wi < nw; ++wi)
+    if (worker_rc[wi] != AGF2_OK) { rc = worker_rc[wi]; h->err = "batch worker set-up failed"; }
+  for (int i = 0; i < nsys; ++i) {
+    if (status) status[i] = st[i];
+    if (st[i] != AGF2_OK && st[i] != AGF2_ERR_NO_CONVERGENCE && rc == AGF2_OK) {
+      rc = st[i];
+      h->err = "system " + std::to_string(i) + ": " + msg[i];
+    }
+  }
+  return rc;
+}
 
 int agf2_get_state(agf2_handle h, double* e, double* C, double* D, int* nqmo) {
   return guarded(h, [&](agf2_context* ctx) {

@@ -32,6 +32,7 @@
 
 #include <algorithm>
 #include <cmath>
+#include <mutex>
 #include <string>
 #include <vector>
 
@@ -73,7 +74,6 @@ struct Params {
   int ksplit;       // MODE_MOMENT: K steps per CTA
   int nsplit;       // MODE_MOMENT: K splits per (tile, moment)
   int ntiles;       // tiles of this launch (the persistent CTAs loop over them)
-  long long kpp;    // MODE_PAIR: K entries of Y per pair (n_cchunks * KCHUNK)
   const int2* pairs;
   const double* e_out;
   const double* e_in;
@@ -81,8 +81,8 @@ struct Params {
   const float* unitA2;  // MOMENT: unit of Yw rows
   const float* unitB;   // MODE_PAIR: unit of Lov rows [i][a];        MOMENT: of Y rows
   int v_stride;         // MODE_PAIR: v (row index of Lov rows is i * v + a)
-  float* Y;            // MODE_PAIR output: FP32 [N][Ks], sliced afterwards
-  float* Yw;           // MODE_PAIR output: FP32 [N][Ks]
+  float* X;            // MODE_PAIR output: FP32 X_xy [N][np][2][ncp] (row stride Ks)
+  int ncp;             // MODE_PAIR: n_cchunks * BN (padded inner count)
   long long Ks;
   long long plane;     // N * Ks
   double* U0;
@@ -106,11 +106,12 @@ __device__ __forceinline__ void load_a(const CUtensorMap* mapA, uint8_t* dst, ui
     tc::tma_load_3d(dst, mapA, bar, ks * BK, s.a_row, limb);
 }
 
-// Work of one tile: up to two K segments into one accumulator set.
+// Work of one tile: one K segment into one accumulator set (nseg = 0: no
+// work, the tile is skipped by every role).
 struct TileWork {
-  Segment seg[2];
+  Segment seg[1];
   int nseg;
-  int p0, c0, q0, moment, pair_local;
+  int p0, c0, q0, moment, pair_local, orient;
   int2 pr;
 };
 
@@ -118,25 +119,32 @@ template <int MODE>
 __device__ __forceinline__ TileWork decode_tile(const Params& P, int t) {
   TileWork w;
   w.nseg = 1;
-  w.p0 = w.c0 = w.q0 = w.moment = w.pair_local = 0;
+  w.p0 = w.c0 = w.q0 = w.moment = w.pair_local = w.orient = 0;
   w.pr = make_int2(0, 0);
   if (MODE == MODE_PAIR) {
+    // ordered pair (x, y) (orient 0) or (y, x) (orient 1) of unordered pair x <= y
     int b = t;
     const int cc = b % P.n_cchunks; b /= P.n_cchunks;
     const int pt = b % P.n_ptiles; b /= P.n_ptiles;
-    w.pair_local = b;
+    w.orient = b & 1;
+    w.pair_local = b >> 1;
     w.pr = P.pairs[P.pair0 + w.pair_local];
     w.p0 = pt * BM;
     w.c0 = cc * BN;
-    w.seg[0] = Segment{w.p0, w.pr.x, w.c0, w.pr.y, 0, 0, P.ksteps, false};
-    w.seg[1] = Segment{w.p0, w.pr.y, w.c0, w.pr.x, 2 * BN, 0, P.ksteps, false};
-    w.nseg = (w.pr.x == w.pr.y) ? 1 : 2;
+    const int xa = w.orient ? w.pr.y : w.pr.x, yb = w.orient ? w.pr.x : w.pr.y;
+    w.seg[0] = Segment{w.p0, xa, w.c0, yb, 0, 0, P.ksteps, false};
+    if (w.orient && w.pr.x == w.pr.y) w.nseg = 0;  // X_yx == X_xy on the diagonal
   } else {
+    // U is symmetric: only tiles with qt >= pt (upper triangle of tiles)
     int b = t;
     const int sp = b % P.nsplit; b /= P.nsplit;
     w.moment = b % 2; b /= 2;
-    const int qt = b % P.n_qtiles; b /= P.n_qtiles;
-    const int pt = b;
+    int pt = 0, qt = 0;
+    for (int r = 0, left = b; r < P.n_ptiles; ++r) {
+      const int row = P.n_ptiles - r;  // tiles qt = r .. n_ptiles - 1
+      if (left < row) { pt = r; qt = r + left; break; }
+      left -= row;
+    }
     w.p0 = pt * BM;
     w.q0 = qt * BN;
     const int kb = sp * P.ksplit;
@@ -151,15 +159,15 @@ __device__ __forceinline__ TileWork decode_tile(const Params& P, int t) {
 //   warp 1: TMEM allocation + single-thread tcgen05.mma issue
 //   warps 2..9: epilogue; warp w reads TMEM lane quarter w % 4 and column
 //   half (w - 2) / 4 of each accumulator
-// MODE_PAIR uses all 512 TMEM columns for one tile's accumulators
-// (X_xy hi/lo, X_yx hi/lo); MODE_MOMENT double-buffers its 256-column
-// accumulator set so a tile's FP64 drain overlaps the next tile's MMAs.
+// Each tile's accumulator set (h0h0 "hi" and correction "lo", BN columns each)
+// takes 256 TMEM columns; two sets are double-buffered so a tile's epilogue
+// overlaps the next tile's MMAs.
 template <int MODE>
 __global__ void __launch_bounds__(NTHREADS, 1)
 gemm6_kernel(const __grid_constant__ CUtensorMap mapA, const __grid_constant__ CUtensorMap mapA2,
              const __grid_constant__ CUtensorMap mapB, const Params P) {
-  constexpr int NBUF = (MODE == MODE_PAIR) ? 1 : 2;
-  constexpr int BUF_COLS = (MODE == MODE_PAIR) ? 4 * BN : 2 * BN;
+  constexpr int NBUF = 2;
+  constexpr int BUF_COLS = 2 * BN;
   constexpr int N_EPI_WARPS = (NTHREADS / 32) - 2;
   extern __shared__ uint8_t smem_raw[];
   uint8_t* smem = reinterpret_cast<uint8_t*>(
@@ -243,8 +251,9 @@ gemm6_kernel(const __grid_constant__ CUtensorMap mapA, const __grid_constant__ C
     const int pb[5] = {0, 1, 2, 0, 1};
     int t = 0, lt = 0;
     bool ok = true;
-    for (int tile = blockIdx.x; tile < P.ntiles && ok; tile += gridDim.x, ++lt) {
+    for (int tile = blockIdx.x; tile < P.ntiles && ok; tile += gridDim.x) {
       const TileWork w = decode_tile<MODE>(P, tile);
+      if (w.nseg == 0) continue;
       const int buf = lt % NBUF;
       const uint32_t use = (uint32_t)(lt / NBUF);
       // wait until the epilogue has drained this accumulator set
@@ -278,6 +287,7 @@ gemm6_kernel(const __grid_constant__ CUtensorMap mapA, const __grid_constant__ C
       }
       tc::umma_commit(&accf_bar[buf]);
       committed_sh = lt + 1;
+      ++lt;
     }
   } else if (warp >= 2) {
     // ---------------- epilogue ----------------
@@ -286,8 +296,9 @@ gemm6_kernel(const __grid_constant__ CUtensorMap mapA, const __grid_constant__ C
     const int r = qd * 32 + lane;
     const int col0 = half * (BN / 2);
     int lt = 0;
-    for (int tile = blockIdx.x; tile < P.ntiles; tile += gridDim.x, ++lt) {
+    for (int tile = blockIdx.x; tile < P.ntiles; tile += gridDim.x) {
       const TileWork w = decode_tile<MODE>(P, tile);
+      if (w.nseg == 0) continue;
       const int buf = lt % NBUF;
       const uint32_t use = (uint32_t)(lt / NBUF);
       if (!tc::mbar_wait(&accf_bar[buf], use & 1, abort_flag)) break;
@@ -295,67 +306,34 @@ gemm6_kernel(const __grid_constant__ CUtensorMap mapA, const __grid_constant__ C
       const uint32_t trow = tmem + buf * BUF_COLS + ((uint32_t)(qd * 32) << 16);
       const int p = w.p0 + r;
       if (MODE == MODE_PAIR) {
-        const int2 pr = w.pr;
-        const bool diag = (pr.x == pr.y);
-        // sqrt(cS), sqrt(cD) as unevaluated float pairs (hi + lo to ~1e-16): a
-        // rounded FP32 constant would enter U^(0) = Y Y^T squared and bias every
-        // diagonal element by up to ~7e-8 relative; with the pair the product is
-        // one round-to-nearest (fmaf) and unbiased.
-        const float sS = diag ? 0.5f : 0.7071067690849304f;
-        const float sS_lo = diag ? 0.0f : 1.2101617485882343e-08f;
-        const float sD = diag ? 0.0f : 1.2247449159622192f;
-        const float sD_lo = diag ? 0.0f : -4.4570629853524224e-08f;
-        const double ex = P.e_out[pr.x] + P.e_out[pr.y];
+        // X[p][pair][orient][c] = (hi + lo) * unit(A row) * unit(B row), FP32
+        const Segment& sg = w.seg[0];
         const bool prow = p < P.N;
-        const float uA1 = prow ? P.unitA[(long long)pr.x * P.N + p] : 0.f;
-        const float uA2 = prow ? P.unitA[(long long)pr.y * P.N + p] : 0.f;
-        // this tile's K range of Y: [kS, kS + BN) for S, [kS + BN, kS + 2 BN) for D
-        const long long kS = (long long)w.pair_local * P.kpp + (long long)(w.c0 / BN) * KCHUNK;
-        // 16 columns per TMEM read; all register indices static (fully unrolled)
+        const float uA = prow ? P.unitA[(long long)sg.a_idx * P.N + p] : 0.f;
+        float* xrow = P.X + (long long)p * P.Ks +
+                      ((long long)w.pair_local * 2 + w.orient) * P.ncp + w.c0;
         for (int cb = col0; cb < col0 + BN / 2; cb += 16) {
-          float h1[16], l1[16], h2[16], l2[16];
-          tc::tmem_ld16(trow + cb, h1);
-          tc::tmem_ld16(trow + BN + cb, l1);
-          if (!diag) {
-            tc::tmem_ld16(trow + 2 * BN + cb, h2);
-            tc::tmem_ld16(trow + 3 * BN + cb, l2);
-          } else {
-#pragma unroll
-            for (int c = 0; c < 16; ++c) { h2[c] = h1[c]; l2[c] = l1[c]; }
-          }
+          float hi[16], lo[16];
+          tc::tmem_ld16(trow + cb, hi);
+          tc::tmem_ld16(trow + BN + cb, lo);
           if (prow) {
-            float* y = P.Y + (long long)p * P.Ks + kS + cb;
-            float* yw = P.Yw + (long long)p * P.Ks + kS + cb;
 #pragma unroll
             for (int g = 0; g < 16; g += 4) {
-              float4 vs, vd, ws, wd;
-              float* pvs = &vs.x; float* pvd = &vd.x; float* pws = &ws.x; float* pwd = &wd.x;
+              float4 o4;
+              float* po = &o4.x;
 #pragma unroll
               for (int c = 0; c < 4; ++c) {
                 const int ci = w.c0 + cb + g + c;
-                float ys = 0.f, yd = 0.f, wt = 0.f;
+                float x = 0.f;
                 if (ci < P.n_in) {
                   // B-row units: hole rows (y, c) -> y*v + c ; particle rows (c, y) -> c*v + y
-                  const long long rb1 = P.hole ? (long long)pr.y * P.v_stride + ci
-                                               : (long long)ci * P.v_stride + pr.y;
-                  const long long rb2 = P.hole ? (long long)pr.x * P.v_stride + ci
-                                               : (long long)ci * P.v_stride + pr.x;
-                  const float xa = (h1[g + c] + l1[g + c]) * (uA1 * P.unitB[rb1]);
-                  const float xb = (h2[g + c] + l2[g + c]) * (uA2 * P.unitB[rb2]);
-                  const float sum = xa + xb, dif = xa - xb;
-                  ys = fmaf(sum, sS, sum * sS_lo);
-                  yd = fmaf(dif, sD, dif * sD_lo);
-                  wt = (float)(ex - P.e_in[ci]);
+                  const long long rb = P.hole ? (long long)sg.b_idx * P.v_stride + ci
+                                              : (long long)ci * P.v_stride + sg.b_idx;
+                  x = (hi[g + c] + lo[g + c]) * (uA * P.unitB[rb]);
                 }
-                pvs[c] = ys;
-                pvd[c] = yd;
-                pws[c] = ys * wt;
-                pwd[c] = yd * wt;
+                po[c] = x;
               }
-              *reinterpret_cast<float4*>(y + g) = vs;
-              *reinterpret_cast<float4*>(y + BN + g) = vd;
-              *reinterpret_cast<float4*>(yw + g) = ws;
-              *reinterpret_cast<float4*>(yw + BN + g) = wd;
+              *reinterpret_cast<float4*>(xrow + cb + g) = o4;
             }
           }
         }
@@ -381,6 +359,7 @@ gemm6_kernel(const __grid_constant__ CUtensorMap mapA, const __grid_constant__ C
       tc::tc_fence_before();
       __syncwarp();
       if (lane == 0) tc::mbar_arrive(&acce_bar[buf]);
+      ++lt;
     }
   }
 
@@ -452,48 +431,109 @@ __global__ void slice_rows_kernel(const T* __restrict__ src, long long nrow, int
   }
 }
 
-// Row maxima of |src| over segments of 4096 columns: maxbits[r] holds the
-// largest |x| of row r as float bits (non-negative floats order like their
-// bit patterns); must be zeroed first.  grid = (segments, rows).
-__global__ void row_absmax_kernel(const float* __restrict__ src, int ncol, long long ld,
-                                  unsigned* __restrict__ maxbits) {
-  __shared__ float sh[8];
-  const long long r = blockIdx.y;
-  const int c0 = blockIdx.x * 4096;
-  const int c1 = min(ncol, c0 + 4096);
-  float m = 0.f;
-  for (int c = c0 + threadIdx.x; c < c1; c += blockDim.x) m = fmaxf(m, fabsf(src[r * ld + c]));
+// Pair-symmetrised operands of GEMM 2 from the pair GEMM's X (Eqs.
+// mp2_zeroth_moment / mp2_first_moment in S/D form): for unordered pair
+// (x, y), inner pole c and row p,
+//   S = X_xy + X_yx, D = X_xy - X_yx, Y_S = sqrt(cS) S, Y_D = sqrt(cD) D,
+//   Yw = (e_x + e_y - e_c) Y.
+// PASS 0 takes each row's max |Y| and |Yw| (atomicMax on the float bits of
+// non-negative values); PASS 1 slices Y and Yw in fixed point with the row's
+// unit into the limb planes, K index pair * kpp + chunk * 256 + (S: c, D: 128 + c).
+// grid = (blocks over pair x inner, N rows).
+struct Combine {
+  const float* X;
+  long long xrow;  // row stride of X
+  int np, ncp, n_in, N, kpp, pair0;
+  const int2* pairs;
+  const double* e_out;
+  const double* e_in;
+  unsigned* maxbits;  // [2][N]
+  __nv_bfloat16* Y;
+  __nv_bfloat16* Yw;
+  long long Ks, plane;
+  float* unitY;
+  float* unitYw;
+};
+
+template <int PASS>
+__global__ void __launch_bounds__(256) combine_kernel(const Combine C) {
+  const int p = blockIdx.y;
+  const long long total = (long long)C.np * C.ncp;
+  const float* xr = C.X + (long long)p * C.xrow;
+  float uy = 1.f, uyw = 1.f;
+  if (PASS == 1) {
+    uy = tc::slice_unitf(__uint_as_float(C.maxbits[p]));
+    uyw = tc::slice_unitf(__uint_as_float(C.maxbits[C.N + p]));
+  }
+  const float iuy = 1.0f / uy, iuyw = 1.0f / uyw;
+  float my = 0.f, mw = 0.f;
+  __nv_bfloat16* yr = C.Y + (long long)p * C.Ks;
+  __nv_bfloat16* ywr = C.Yw + (long long)p * C.Ks;
+  for (long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x; e < total;
+       e += (long long)gridDim.x * blockDim.x) {
+    const int pl = (int)(e / C.ncp), c = (int)(e - (long long)pl * C.ncp);
+    const int2 pr = C.pairs[C.pair0 + pl];
+    const bool diag = pr.x == pr.y;
+    float ys = 0.f, yd = 0.f, wt = 0.f;
+    if (c < C.n_in) {
+      const float x0 = xr[(2LL * pl) * C.ncp + c];
+      const float x1 = diag ? x0 : xr[(2LL * pl + 1) * C.ncp + c];
+      // sqrt(cS), sqrt(cD) as unevaluated float pairs: a rounded FP32 constant
+      // would enter U^(0) = Y Y^T squared and bias its diagonal (~7e-8)
+      const float sS = diag ? 0.5f : 0.7071067690849304f;
+      const float sS_lo = diag ? 0.0f : 1.2101617485882343e-08f;
+      const float sD = diag ? 0.0f : 1.2247449159622192f;
+      const float sD_lo = diag ? 0.0f : -4.4570629853524224e-08f;
+      const float sum = x0 + x1, dif = x0 - x1;
+      ys = fmaf(sum, sS, sum * sS_lo);
+      yd = fmaf(dif, sD, dif * sD_lo);
+      wt = (float)(C.e_out[pr.x] + C.e_out[pr.y] - C.e_in[c]);
+    }
+    const float yws = ys * wt, ywd = yd * wt;
+    if (PASS == 0) {
+      my = fmaxf(my, fmaxf(fabsf(ys), fabsf(yd)));
+      mw = fmaxf(mw, fmaxf(fabsf(yws), fabsf(ywd)));
+    } else {
+      const long long k = (long long)pl * C.kpp + (c / BN) * KCHUNK + (c % BN);
+      __nv_bfloat16 h0, h1, h2;
+      tc::slice3f(ys * iuy, h0, h1, h2);
+      yr[k] = h0; yr[C.plane + k] = h1; yr[2 * C.plane + k] = h2;
+      tc::slice3f(yd * iuy, h0, h1, h2);
+      yr[k + BN] = h0; yr[C.plane + k + BN] = h1; yr[2 * C.plane + k + BN] = h2;
+      tc::slice3f(yws * iuyw, h0, h1, h2);
+      ywr[k] = h0; ywr[C.plane + k] = h1; ywr[2 * C.plane + k] = h2;
+      tc::slice3f(ywd * iuyw, h0, h1, h2);
+      ywr[k + BN] = h0; ywr[C.plane + k + BN] = h1; ywr[2 * C.plane + k + BN] = h2;
+    }
+  }
+  if (PASS == 0) {
+    __shared__ float shy[8], shw[8];
 #pragma unroll
-  for (int o = 16; o > 0; o >>= 1) m = fmaxf(m, __shfl_xor_sync(0xffffffffu, m, o));
-  if ((threadIdx.x & 31) == 0) sh[threadIdx.x >> 5] = m;
-  __syncthreads();
-  if (threadIdx.x == 0) {
-    for (int w = 1; w < (int)(blockDim.x >> 5); ++w) m = fmaxf(m, sh[w]);
-    atomicMax(maxbits + r, __float_as_uint(m));
+    for (int o = 16; o > 0; o >>= 1) {
+      my = fmaxf(my, __shfl_xor_sync(0xffffffffu, my, o));
+      mw = fmaxf(mw, __shfl_xor_sync(0xffffffffu, mw, o));
+    }
+    if ((threadIdx.x & 31) == 0) { shy[threadIdx.x >> 5] = my; shw[threadIdx.x >> 5] = mw; }
+    __syncthreads();
+    if (threadIdx.x == 0) {
+      for (int w = 1; w < (int)(blockDim.x >> 5); ++w) { my = fmaxf(my, shy[w]); mw = fmaxf(mw, shw[w]); }
+      atomicMax(C.maxbits + p, __float_as_uint(my));
+      atomicMax(C.maxbits + C.N + p, __float_as_uint(mw));
+    }
+  } else if (blockIdx.x == 0 && threadIdx.x == 0) {
+    C.unitY[p] = uy;
+    C.unitYw[p] = uyw;
   }
 }
 
-// Fixed-point three-limb slicing of FP32 rows with each row's unit from its
-// exact maximum (row_absmax_kernel); element-parallel.  Writes limb planes
-// [3][nrow][ncolp] (zero beyond ncol) and the unit of every row.
-__global__ void slice_fp32_kernel(const float* __restrict__ src, long long nrow, int ncol,
-                                  long long ld, int ncolp, const unsigned* __restrict__ maxbits,
-                                  __nv_bfloat16* __restrict__ dst, float* __restrict__ unit) {
-  const long long total = nrow * (long long)ncolp;
+// Lower off-diagonal tiles of U (never computed) <- their upper mirror.
+__global__ void mirror_tiles_kernel(double* U, int N, int nmat) {
+  const long long total = (long long)nmat * N * N;
   for (long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x; t < total;
        t += (long long)gridDim.x * blockDim.x) {
-    const long long r = t / ncolp;
-    const int c = (int)(t - r * ncolp);
-    // FP32 throughout (GB300's FP64 rate is a small fraction of FP32); exact:
-    // the unit is a power of two and slice3f's residuals are exact
-    const float u = tc::slice_unitf(__uint_as_float(maxbits[r]));
-    const float x = (c < ncol) ? src[r * ld + c] : 0.0f;
-    __nv_bfloat16 h0, h1, h2;
-    tc::slice3f(x * (1.0f / u), h0, h1, h2);
-    dst[t] = h0;
-    dst[total + t] = h1;
-    dst[2 * total + t] = h2;
-    if (c == 0) unit[r] = u;
+    const long long m = t / ((long long)N * N);
+    const int p = (int)((t / N) % N), q = (int)(t % N);
+    if (p / BM > q / BN) U[m * N * N + (long long)p * N + q] = U[m * N * N + (long long)q * N + p];
   }
 }
 
@@ -542,7 +582,8 @@ struct MixedWs {
   Buffers u_xo, u_xv, u_ov, u_y, u_yw, y32, yw32, maxbits;
 };
 
-MixedWs g_ws[64];  // per device
+std::mutex g_attr_mu;
+bool g_attr_done[64] = {false};
 
 template <class T>
 T* grow(Buffers& b, size_t count, std::string& err) {
@@ -564,10 +605,21 @@ T* grow(Buffers& b, size_t count, std::string& err) {
 
 }  // namespace
 
+void* mixed_workspace_create() { return new MixedWs(); }
+
+void mixed_workspace_destroy(void* w) {
+  if (!w) return;
+  MixedWs* W = static_cast<MixedWs*>(w);
+  for (Buffers* b : {&W->lx_o, &W->lx_v, &W->l_ov, &W->y, &W->yw, &W->pairs, &W->err, &W->u_xo,
+                     &W->u_xv, &W->u_ov, &W->u_y, &W->u_yw, &W->y32, &W->yw32, &W->maxbits})
+    if (b->p) cudaFree(b->p);
+  delete W;
+}
+
 int mixed_build_moments_rotated(const double* Lxo, const double* Lxv, const double* Lov, int naux,
                                 int N, int o, int v, const double* eo, const double* ev,
                                 double* U_hole, double* U_part, std::string& err,
-                                cudaStream_t s, KernelStats* stats) {
+                                cudaStream_t s, KernelStats* stats, void* workspace) {
   // CUDA events around the tcgen05 launches when stats->enabled
   std::vector<cudaEvent_t> evs;
   std::vector<int> ev_kind;
@@ -589,17 +641,19 @@ int mixed_build_moments_rotated(const double* Lxo, const double* Lxv, const doub
   };
   int dev = 0;
   cudaGetDevice(&dev);
-  MixedWs& W = g_ws[dev & 63];
-  static bool attr_done[64] = {false};
-  if (!attr_done[dev & 63]) {
-    if (cudaFuncSetAttribute(gemm6_kernel<MODE_PAIR>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                             SMEM_BYTES) != cudaSuccess ||
-        cudaFuncSetAttribute(gemm6_kernel<MODE_MOMENT>,
-                             cudaFuncAttributeMaxDynamicSharedMemorySize, SMEM_BYTES) != cudaSuccess) {
-      err = "cudaFuncSetAttribute(smem) failed";
-      return AGF2_ERR_CUDA;
+  MixedWs& W = *static_cast<MixedWs*>(workspace);
+  {
+    std::lock_guard<std::mutex> attr_lock(g_attr_mu);
+    if (!g_attr_done[dev & 63]) {
+      if (cudaFuncSetAttribute(gemm6_kernel<MODE_PAIR>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                               SMEM_BYTES) != cudaSuccess ||
+          cudaFuncSetAttribute(gemm6_kernel<MODE_MOMENT>,
+                               cudaFuncAttributeMaxDynamicSharedMemorySize, SMEM_BYTES) != cudaSuccess) {
+        err = "cudaFuncSetAttribute(smem) failed";
+        return AGF2_ERR_CUDA;
+      }
+      g_attr_done[dev & 63] = true;
     }
-    attr_done[dev & 63] = true;
   }
   int nsm = 148;
   cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev);
@@ -669,27 +723,30 @@ int mixed_build_moments_rotated(const double* Lxo, const double* Lxv, const doub
     if (!dpairs) return AGF2_ERR_OOM;
     cudaMemcpyAsync(dpairs, pairs.data(), pairs.size() * sizeof(int2), cudaMemcpyHostToDevice, s);
     const int n_cchunks = (n_in + BN - 1) / BN;
+    const int ncp = n_cchunks * BN;
     const long long kpp = (long long)n_cchunks * KCHUNK;
-    // pairs per block: Y + Yw limb planes of the block stay near L2 size, and the
-    // block's tile count is a whole number of waves of the persistent CTAs
-    const double per_pair = (double)N * kpp * 2 /*Y,Yw*/ * 3 /*limbs*/ * 2 /*bytes*/;
-    const int tpp = n_ptiles * n_cchunks;  // tiles per pair
-    int bp = (int)std::max(1.0, std::floor(96.0e6 / per_pair));
+    // pairs per block: large enough that GEMM 2's split-K tiles are long (each
+    // tile ends in a 128x128 FP64 drain), about 256 MB of X + Y + Yw, and a
+    // whole number of waves of the persistent CTAs
+    const double per_pair = (double)N * (kpp * 2 /*Y,Yw*/ * 3 /*limbs*/ * 2 /*bytes*/ +
+                                         2.0 * ncp * 4 /*X, both orders*/);
+    const int tpp = 2 * n_ptiles * n_cchunks;  // tiles per unordered pair
+    int bp = (int)std::max(1.0, std::floor(256.0e6 / per_pair));
     {
       int g = nsm, t = tpp;
       while (t) { const int r = g % t; g = t; t = r; }  // gcd(nsm, tpp)
       const int unit = nsm / g;                          // pairs per whole wave
-      const int bp_lim = (int)std::floor(160.0e6 / per_pair);
+      const int bp_lim = (int)std::floor(384.0e6 / per_pair);
       if (unit <= bp_lim) bp = std::max(unit, bp / unit * unit);
     }
     bp = std::max(1, std::min<int>(bp, (int)pairs.size()));
     const long long Ks = (long long)bp * kpp;
+    const long long Kx = (long long)bp * 2 * ncp;  // row length of X
     __nv_bfloat16* y = grow<__nv_bfloat16>(W.y, 3LL * N * Ks, err);
     __nv_bfloat16* yw = grow<__nv_bfloat16>(W.yw, 3LL * N * Ks, err);
-    float* y32 = grow<float>(W.y32, (size_t)N * Ks, err);
-    float* yw32 = grow<float>(W.yw32, (size_t)N * Ks, err);
+    float* x32 = grow<float>(W.y32, (size_t)N * Kx, err);
     unsigned* maxbits = grow<unsigned>(W.maxbits, 2 * (size_t)N, err);
-    if (!y || !yw || !y32 || !yw32 || !maxbits) return AGF2_ERR_OOM;
+    if (!y || !yw || !x32 || !maxbits) return AGF2_ERR_OOM;
     for (size_t b0 = 0; b0 < pairs.size(); b0 += bp) {
       const int np = (int)std::min<size_t>(bp, pairs.size() - b0);
       const long long K = (long long)np * kpp;
@@ -702,20 +759,18 @@ int mixed_build_moments_rotated(const double* Lxo, const double* Lxv, const doub
       P.n_out = n_out;
       P.hole = hole ? 1 : 0;
       P.pair0 = (int)b0;
-      P.kpp = kpp;
       P.pairs = dpairs;
       P.e_out = e_out;
       P.e_in = e_in;
       P.unitA = hole ? u_xo : u_xv;
       P.unitB = u_ov;
       P.v_stride = v;
-      P.Y = y32;
-      P.Yw = yw32;
-      P.Ks = Ks;
-      P.plane = (long long)N * Ks;
+      P.X = x32;
+      P.ncp = ncp;
+      P.Ks = Kx;
       P.err = derr;
-      const int grid1 = std::min(np * n_ptiles * n_cchunks, nsm);
-      P.ntiles = np * n_ptiles * n_cchunks;
+      P.ntiles = np * tpp;
+      const int grid1 = std::min(P.ntiles, nsm);
       // algorithmic flops: GEMM 1 for the ordered pairs of this block
       long long ordered = 0;
       for (int t = 0; t < np; ++t) ordered += (pairs[b0 + t].x == pairs[b0 + t].y) ? 1 : 2;
@@ -724,15 +779,16 @@ int mixed_build_moments_rotated(const double* Lxo, const double* Lxv, const doub
           hole ? map_xo : map_xv, hole ? map_xo : map_xv, hole ? map_b_hole : map_b_part, P);
       mark_end();
       count_launch();
-      // fixed-point limbs of Y and Yw with each row's unit from its exact maximum
+      // S/D and energy weights, then fixed-point limbs with each row's exact unit
+      Combine C{x32, Kx, np, ncp, n_in, N, (int)kpp, (int)b0, dpairs, e_out, e_in, maxbits,
+                y, yw, Ks, (long long)N * Ks, u_y, u_yw};
       cudaMemsetAsync(maxbits, 0, 2 * N * sizeof(unsigned), s);
-      const dim3 gmax((unsigned)((K + 4095) / 4096), (unsigned)N);
-      row_absmax_kernel<<<gmax, 256, 0, s>>>(y32, (int)K, Ks, maxbits);
-      row_absmax_kernel<<<gmax, 256, 0, s>>>(yw32, (int)K, Ks, maxbits + N);
-      const int gsl = (int)std::min<long long>(((long long)N * Ks + 255) / 256, 152LL * 32);
-      slice_fp32_kernel<<<gsl, 256, 0, s>>>(y32, N, (int)K, Ks, (int)Ks, maxbits, y, u_y);
-      slice_fp32_kernel<<<gsl, 256, 0, s>>>(yw32, N, (int)K, Ks, (int)Ks, maxbits + N, yw, u_yw);
-      count_launch(4);
+      const long long per_row = (long long)np * ncp;
+      const dim3 gc((unsigned)std::max(1LL, std::min<long long>((per_row + 2047) / 2048, 64)),
+                    (unsigned)N);
+      combine_kernel<0><<<gc, 256, 0, s>>>(C);
+      combine_kernel<1><<<gc, 256, 0, s>>>(C);
+      count_launch(2);
       // GEMM 2 over this block's K = np * kpp
       CUtensorMap map_y, map_yw;
       cuuint64_t dims[3] = {(cuuint64_t)K, (cuuint64_t)N, 3};
@@ -745,7 +801,7 @@ int mixed_build_moments_rotated(const double* Lxo, const double* Lxv, const doub
       M.n_ptiles = n_ptiles;
       M.n_qtiles = (N + BN - 1) / BN;
       M.ksteps = (int)((K + BK - 1) / BK);
-      const int tiles = M.n_ptiles * M.n_qtiles * 2;
+      const int tiles = M.n_ptiles * (M.n_ptiles + 1) / 2 * 2;  // upper tiles x 2 moments
       // about two tiles per persistent CTA, so each drain overlaps the next tile's MMAs
       int nsplit = std::max(1, (nsm * 2 + tiles - 1) / tiles);
       nsplit = std::min(nsplit, M.ksteps);
@@ -771,6 +827,13 @@ int mixed_build_moments_rotated(const double* Lxo, const double* Lxv, const doub
         return AGF2_ERR_CUDA;
       }
     }
+  }
+  {
+    const long long tot = 2LL * N * N;
+    const int g = (int)std::min<long long>((tot + 255) / 256, 152LL * 32);
+    mirror_tiles_kernel<<<g, 256, 0, s>>>(U_hole, N, 2);
+    mirror_tiles_kernel<<<g, 256, 0, s>>>(U_part, N, 2);
+    count_launch(2);
   }
   int herr = 0;
   cudaMemcpyAsync(&herr, derr, sizeof(int), cudaMemcpyDeviceToHost, s);

@@ -253,3 +253,15 @@ def test_slice_additivity():
     Bh, _ = O.build_moments_loops(s.L, e, C, mu)
     Uh, _ = O.build_moments(s.L, e, C, mu)
     assert rel(Uh[0], 0.5 * (Bh[0] + Bh[0].T)) < 1e-12
+
+
+def test_moment_elements_match_full_build():
+    s = make_system(9, 2, 11, 71)
+    e, C, mu = random_poles(9, 22, 8, 71)
+    Uh, Up = O.build_moments(s.L, e, C, mu)
+    pq = [(0, 0), (3, 7), (8, 2), (5, 5)]
+    eh, ep = O.moment_elements(s.L, e, C, mu, pq)
+    for t, (p, q) in enumerate(pq):
+        for n in range(2):
+            assert abs(eh[t, n] - Uh[n, p, q]) <= 1e-12 * np.max(np.abs(Uh[n]))
+            assert abs(ep[t, n] - Up[n, p, q]) <= 1e-12 * np.max(np.abs(Up[n]))
