@@ -337,6 +337,7 @@ gemm6_kernel(const __grid_constant__ CUtensorMap mapA, const __grid_constant__ C
             }
           }
         }
+
       } else {
         double* U = w.moment == 0 ? P.U0 : P.U1;
         const double uA = (p < P.N) ? (double)(w.moment == 0 ? P.unitA : P.unitA2)[p] : 0.0;
@@ -436,10 +437,13 @@ __global__ void slice_rows_kernel(const T* __restrict__ src, long long nrow, int
 // (x, y), inner pole c and row p,
 //   S = X_xy + X_yx, D = X_xy - X_yx, Y_S = sqrt(cS) S, Y_D = sqrt(cD) D,
 //   Yw = (e_x + e_y - e_c) Y.
-// PASS 0 takes each row's max |Y| and |Yw| (atomicMax on the float bits of
-// non-negative values); PASS 1 slices Y and Yw in fixed point with the row's
-// unit into the limb planes, K index pair * kpp + chunk * 256 + (S: c, D: 128 + c).
-// grid = (blocks over pair x inner, N rows).
+// PASS 0 takes each row's exact max |Y| and |Yw| over the block (atomicMax on
+// the float bits of non-negative values); PASS 1 slices Y and Yw in fixed
+// point with those units into the limb planes at K index
+// pair * kpp + chunk * 256 + (S: c, D: 128 + c).  Exact maxima matter: a unit
+// from a bound (e.g. sqrt(6) max|X|) coarsens the grid and the squared
+// rounding error biases diag U^(0) (measured +1e-8 relative).  Four
+// consecutive c per thread; grid = (blocks over pair x inner / 4, N rows).
 struct Combine {
   const float* X;
   long long xrow;  // row stride of X
@@ -447,7 +451,7 @@ struct Combine {
   const int2* pairs;
   const double* e_out;
   const double* e_in;
-  unsigned* maxbits;  // [2][N]
+  unsigned* maxbits;  // [2][N]: |Y|, |Yw|
   __nv_bfloat16* Y;
   __nv_bfloat16* Yw;
   long long Ks, plane;
@@ -455,11 +459,24 @@ struct Combine {
   float* unitYw;
 };
 
+__device__ __forceinline__ void store4(__nv_bfloat16* base, long long plane, long long k,
+                                       const __nv_bfloat16 (&h)[3][4]) {
+#pragma unroll
+  for (int l = 0; l < 3; ++l) {
+    __nv_bfloat162 a = __halves2bfloat162(h[l][0], h[l][1]);
+    __nv_bfloat162 b = __halves2bfloat162(h[l][2], h[l][3]);
+    uint2 u;
+    u.x = *reinterpret_cast<uint32_t*>(&a);
+    u.y = *reinterpret_cast<uint32_t*>(&b);
+    *reinterpret_cast<uint2*>(base + l * plane + k) = u;
+  }
+}
+
 template <int PASS>
 __global__ void __launch_bounds__(256) combine_kernel(const Combine C) {
   const int p = blockIdx.y;
-  const long long total = (long long)C.np * C.ncp;
-  const float* xr = C.X + (long long)p * C.xrow;
+  const int nq = C.ncp / 4;  // groups of 4 inner poles per pair
+  const int total = C.np * nq;
   float uy = 1.f, uyw = 1.f;
   if (PASS == 1) {
     uy = tc::slice_unitf(__uint_as_float(C.maxbits[p]));
@@ -467,43 +484,56 @@ __global__ void __launch_bounds__(256) combine_kernel(const Combine C) {
   }
   const float iuy = 1.0f / uy, iuyw = 1.0f / uyw;
   float my = 0.f, mw = 0.f;
+  const float* xr = C.X + (long long)p * C.xrow;
   __nv_bfloat16* yr = C.Y + (long long)p * C.Ks;
   __nv_bfloat16* ywr = C.Yw + (long long)p * C.Ks;
-  for (long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x; e < total;
-       e += (long long)gridDim.x * blockDim.x) {
-    const int pl = (int)(e / C.ncp), c = (int)(e - (long long)pl * C.ncp);
+  for (int e = blockIdx.x * blockDim.x + threadIdx.x; e < total; e += gridDim.x * blockDim.x) {
+    const int pl = e / nq, c0 = (e - pl * nq) * 4;
     const int2 pr = C.pairs[C.pair0 + pl];
     const bool diag = pr.x == pr.y;
-    float ys = 0.f, yd = 0.f, wt = 0.f;
-    if (c < C.n_in) {
-      const float x0 = xr[(2LL * pl) * C.ncp + c];
-      const float x1 = diag ? x0 : xr[(2LL * pl + 1) * C.ncp + c];
-      // sqrt(cS), sqrt(cD) as unevaluated float pairs: a rounded FP32 constant
-      // would enter U^(0) = Y Y^T squared and bias its diagonal (~7e-8)
-      const float sS = diag ? 0.5f : 0.7071067690849304f;
-      const float sS_lo = diag ? 0.0f : 1.2101617485882343e-08f;
-      const float sD = diag ? 0.0f : 1.2247449159622192f;
-      const float sD_lo = diag ? 0.0f : -4.4570629853524224e-08f;
-      const float sum = x0 + x1, dif = x0 - x1;
-      ys = fmaf(sum, sS, sum * sS_lo);
-      yd = fmaf(dif, sD, dif * sD_lo);
-      wt = (float)(C.e_out[pr.x] + C.e_out[pr.y] - C.e_in[c]);
+    const float4 x0 = *reinterpret_cast<const float4*>(xr + (2LL * pl) * C.ncp + c0);
+    const float4 x1 = diag ? x0 : *reinterpret_cast<const float4*>(xr + (2LL * pl + 1) * C.ncp + c0);
+    // sqrt(cS), sqrt(cD) as unevaluated float pairs: a rounded FP32 constant
+    // would enter U^(0) = Y Y^T squared and bias its diagonal (~7e-8)
+    const float sS = diag ? 0.5f : 0.7071067690849304f;
+    const float sS_lo = diag ? 0.0f : 1.2101617485882343e-08f;
+    const float sD = diag ? 0.0f : 1.2247449159622192f;
+    const float sD_lo = diag ? 0.0f : -4.4570629853524224e-08f;
+    const double ex = C.e_out[pr.x] + C.e_out[pr.y];
+    const float a0[4] = {x0.x, x0.y, x0.z, x0.w};
+    const float a1[4] = {x1.x, x1.y, x1.z, x1.w};
+    float ys[4], yd[4], wt[4];
+#pragma unroll
+    for (int j = 0; j < 4; ++j) {
+      const int c = c0 + j;
+      ys[j] = yd[j] = wt[j] = 0.f;
+      if (c < C.n_in) {
+        const float sum = a0[j] + a1[j], dif = a0[j] - a1[j];
+        ys[j] = fmaf(sum, sS, sum * sS_lo);
+        yd[j] = fmaf(dif, sD, dif * sD_lo);
+        wt[j] = (float)(ex - C.e_in[c]);
+      }
     }
-    const float yws = ys * wt, ywd = yd * wt;
     if (PASS == 0) {
-      my = fmaxf(my, fmaxf(fabsf(ys), fabsf(yd)));
-      mw = fmaxf(mw, fmaxf(fabsf(yws), fabsf(ywd)));
+#pragma unroll
+      for (int j = 0; j < 4; ++j) {
+        my = fmaxf(my, fmaxf(fabsf(ys[j]), fabsf(yd[j])));
+        mw = fmaxf(mw, fmaxf(fabsf(ys[j] * wt[j]), fabsf(yd[j] * wt[j])));
+      }
     } else {
-      const long long k = (long long)pl * C.kpp + (c / BN) * KCHUNK + (c % BN);
-      __nv_bfloat16 h0, h1, h2;
-      tc::slice3f(ys * iuy, h0, h1, h2);
-      yr[k] = h0; yr[C.plane + k] = h1; yr[2 * C.plane + k] = h2;
-      tc::slice3f(yd * iuy, h0, h1, h2);
-      yr[k + BN] = h0; yr[C.plane + k + BN] = h1; yr[2 * C.plane + k + BN] = h2;
-      tc::slice3f(yws * iuyw, h0, h1, h2);
-      ywr[k] = h0; ywr[C.plane + k] = h1; ywr[2 * C.plane + k] = h2;
-      tc::slice3f(ywd * iuyw, h0, h1, h2);
-      ywr[k + BN] = h0; ywr[C.plane + k + BN] = h1; ywr[2 * C.plane + k + BN] = h2;
+      __nv_bfloat16 hs[3][4], hd[3][4], ws[3][4], wd[3][4];
+#pragma unroll
+      for (int j = 0; j < 4; ++j) {
+        tc::slice3f(ys[j] * iuy, hs[0][j], hs[1][j], hs[2][j]);
+        tc::slice3f(yd[j] * iuy, hd[0][j], hd[1][j], hd[2][j]);
+        tc::slice3f(ys[j] * wt[j] * iuyw, ws[0][j], ws[1][j], ws[2][j]);
+        tc::slice3f(yd[j] * wt[j] * iuyw, wd[0][j], wd[1][j], wd[2][j]);
+      }
+      const long long k = (long long)pl * C.kpp + (c0 / BN) * KCHUNK + (c0 % BN);
+      store4(yr, C.plane, k, hs);
+      store4(yr, C.plane, k + BN, hd);
+      store4(ywr, C.plane, k, ws);
+      store4(ywr, C.plane, k + BN, wd);
     }
   }
   if (PASS == 0) {
@@ -770,6 +800,7 @@ int mixed_build_moments_rotated(const double* Lxo, const double* Lxv, const doub
       P.Ks = Kx;
       P.err = derr;
       P.ntiles = np * tpp;
+
       const int grid1 = std::min(P.ntiles, nsm);
       // algorithmic flops: GEMM 1 for the ordered pairs of this block
       long long ordered = 0;
@@ -783,8 +814,8 @@ int mixed_build_moments_rotated(const double* Lxo, const double* Lxv, const doub
       Combine C{x32, Kx, np, ncp, n_in, N, (int)kpp, (int)b0, dpairs, e_out, e_in, maxbits,
                 y, yw, Ks, (long long)N * Ks, u_y, u_yw};
       cudaMemsetAsync(maxbits, 0, 2 * N * sizeof(unsigned), s);
-      const long long per_row = (long long)np * ncp;
-      const dim3 gc((unsigned)std::max(1LL, std::min<long long>((per_row + 2047) / 2048, 64)),
+      const long long per_row = (long long)np * ncp / 4;
+      const dim3 gc((unsigned)std::max(1LL, std::min<long long>((per_row + 1023) / 1024, 64)),
                     (unsigned)N);
       combine_kernel<0><<<gc, 256, 0, s>>>(C);
       combine_kernel<1><<<gc, 256, 0, s>>>(C);

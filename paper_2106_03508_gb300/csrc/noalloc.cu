@@ -187,8 +187,8 @@ extern "C" int agf2_build_moments_noalloc(const double* L, int naux, int nmo, co
     const double* e_out;
     const double* e_in;
     double* U;
-  } secs[2] = {{o, v, Lxo, Lov, (long long)v * Q, (long long)Q, eo, ev, U_hole},
-               {v, o, Lxv, Lov, (long long)Q, (long long)v * Q, ev, eo, U_part}};
+  } secs[2] = {{o, v, Lxo, Lov, (long long)v * (long long)Q, (long long)Q, eo, ev, U_hole},
+               {v, o, Lxv, Lov, (long long)Q, (long long)v * (long long)Q, ev, eo, U_part}};
   for (const Sec& S : secs) {
     const int nbs = std::min(nb, S.n_out);
     for (int I0 = 0; I0 < S.n_out; I0 += nbs) {
