@@ -46,8 +46,8 @@ namespace {
 
 constexpr int BM = 128;         // MMA M (rows of p)
 constexpr int BN = 128;         // MMA N
-constexpr int BK = 64;          // K elements per stage (128 B rows)
-constexpr int STAGES = 2;
+constexpr int BK = 32;          // K elements per stage (64 B rows, 64-byte swizzle)
+constexpr int STAGES = 4;       // 4 x 48 KB: three stages in flight while one is consumed
 constexpr int TILE_A = BM * BK * 2;     // bytes of one A limb tile
 constexpr int TILE_B = BN * BK * 2;     // bytes of one B limb tile
 constexpr int STAGE_BYTES = 3 * TILE_A + 3 * TILE_B;
@@ -274,12 +274,12 @@ gemm6_kernel(const __grid_constant__ CUtensorMap mapA, const __grid_constant__ C
             const uint32_t acc = (ks > s.kbeg || kk > 0) ? 1u : 0u;
 #pragma unroll
             for (int pi = 0; pi < 5; ++pi) {
-              const uint64_t ad = tc::sdesc_sw128(base + pa[pi] * TILE_A + kk * 32);
-              const uint64_t bd = tc::sdesc_sw128(base + 3 * TILE_A + pb[pi] * TILE_B + kk * 32);
+              const uint64_t ad = tc::sdesc_sw64(base + pa[pi] * TILE_A + kk * 32);
+              const uint64_t bd = tc::sdesc_sw64(base + 3 * TILE_A + pb[pi] * TILE_B + kk * 32);
               tc::umma_bf16(acc_lo, ad, bd, idesc, (acc || pi > 0) ? 1u : 0u);
             }
-            tc::umma_bf16(acc_hi, tc::sdesc_sw128(base + kk * 32),
-                          tc::sdesc_sw128(base + 3 * TILE_A + kk * 32), idesc, acc);
+            tc::umma_bf16(acc_hi, tc::sdesc_sw64(base + kk * 32),
+                          tc::sdesc_sw64(base + 3 * TILE_A + kk * 32), idesc, acc);
           }
           tc::umma_commit(&empty_bar[st]);
           consumed_sh = t + 1;
@@ -593,7 +593,7 @@ bool make_map(CUtensorMap* m, const void* base, int rank, const cuuint64_t* dims
   cuuint32_t es[5] = {1, 1, 1, 1, 1};
   CUresult r = enc(m, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, rank, const_cast<void*>(base), dims,
                    strides_bytes, box, es, CU_TENSOR_MAP_INTERLEAVE_NONE,
-                   CU_TENSOR_MAP_SWIZZLE_128B, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
+                   CU_TENSOR_MAP_SWIZZLE_64B, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
                    CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
   if (r != CUDA_SUCCESS) {
     err = "cuTensorMapEncodeTiled failed (" + std::to_string((int)r) + ")";

@@ -1,8 +1,9 @@
 // tcgen05 / TMA / mbarrier building blocks for sm_103a (inline PTX).
 //
 // Conventions of the split-BF16 GEMM mainloop used by the moment build:
-//  - operands are K-major BF16 tiles of 64 K-elements (128 B rows) loaded by
-//    TMA with 128-byte swizzling; an 8-row swizzle atom is 1024 B;
+//  - operands are K-major BF16 tiles loaded by TMA with 128-byte (64 K
+//    elements per row, 1024 B atoms) or 64-byte (32 per row, 512 B atoms)
+//    swizzling;
 //  - one elected thread issues tcgen05.mma (kind::f16, BF16 inputs, FP32
 //    accumulator in tensor memory), M = 128 rows, N = BN columns, K = 16 per
 //    instruction;
@@ -132,6 +133,18 @@ __device__ __forceinline__ uint64_t sdesc_sw128(uint32_t saddr) {
   d |= (uint64_t)(1024u >> 4) << 32;  // stride byte offset
   d |= (uint64_t)1 << 46;             // descriptor version
   d |= (uint64_t)2 << 61;             // SWIZZLE_128B
+  return d;
+}
+
+// Same for 64-byte swizzled K-major tiles (rows of 64 B = 32 BF16, 8-row atoms
+// of 512 B).
+__device__ __forceinline__ uint64_t sdesc_sw64(uint32_t saddr) {
+  uint64_t d = 0;
+  d |= (uint64_t)((saddr & 0x3FFFFu) >> 4);
+  d |= (uint64_t)1 << 16;             // leading byte offset (unused for this layout)
+  d |= (uint64_t)(512u >> 4) << 32;   // stride byte offset
+  d |= (uint64_t)1 << 46;             // descriptor version
+  d |= (uint64_t)4 << 61;             // SWIZZLE_64B
   return d;
 }
 
