@@ -219,6 +219,19 @@ int agf2_run_batched(agf2_handle h, int nsys, const agf2_system* systems, const 
 int agf2_get_state(agf2_handle h, double* e, double* C, double* D, int* nqmo);
 
 /*
+ * Spectral function of the Green's function (the broadened spectra of the
+ * paper's artemisinin figure, eta = 0.2 eV there):
+ *   A_p(w) = -(1/pi) Im G_pp(w + i eta) = (1/pi) sum_x C[p][x]^2 eta / ((w - e_x)^2 + eta^2),
+ *   A(w)   = sum_p A_p(w)  (the trace).
+ *   e [nqmo], C [nmo][nqmo]: poles and couplings (e.g. from agf2_get_state)
+ *   omega [nomega]: frequencies (Ha); eta > 0 (Ha)
+ *   A_total [nomega] out; A_orb [nmo][nomega] out or NULL
+ */
+int agf2_spectral_function(agf2_handle h, const double* e, const double* C, int nmo, int nqmo,
+                           const double* omega, int nomega, double eta, double* A_total,
+                           double* A_orb);
+
+/*
  * Opt-in timing of the split-precision tensor-core kernels: with enable = 1
  * every launch of the pair GEMM (kind 0: GEMM 1 of the moment build with its
  * S/D and energy-weight epilogue) and of the moment GEMM (kind 1: GEMM 2 into

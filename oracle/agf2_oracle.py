@@ -490,6 +490,15 @@ def run(h, L, nelec, eps0, max_iter=50, conv_tol=1e-8, nmom=1, fock_tol=1e-10,
                      it, converged, e, C, D, hist, moms)
 
 
+def spectral_function(e, C, omega, eta):
+    """A_p(w) = -(1/pi) Im G_pp(w + i eta) = (1/pi) sum_x C_px^2 eta / ((w - e_x)^2 + eta^2)
+    for the physical orbitals p, and A(w) = sum_p A_p(w) (the trace; the
+    broadened spectra of the paper's artemisinin figure).  Returns (A [nw], A_orb [N, nw])."""
+    lor = eta / np.pi / ((omega[None, :] - e[:, None]) ** 2 + eta ** 2)   # [x, w]
+    A_orb = (C * C) @ lor
+    return A_orb.sum(axis=0), A_orb
+
+
 def flops_moments(nmo, nocc_poles, nvir_poles, naux, nmom=1):
     """Algorithmic flop count of one moment build (both sectors)."""
     o, v = nocc_poles, nvir_poles

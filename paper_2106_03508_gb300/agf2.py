@@ -31,7 +31,7 @@ EXPORTED = [
     "agf2_hcore_from_mo_energies", "agf2_build_moments", "agf2_compress",
     "agf2_fock_opts_default", "agf2_fock_loop", "agf2_opts_default", "agf2_run",
     "agf2_get_state", "agf2_set_profiling", "agf2_kernel_stats", "agf2_launch_count",
-    "agf2_build_moments_noalloc", "agf2_run_batched",
+    "agf2_build_moments_noalloc", "agf2_run_batched", "agf2_spectral_function",
 ]
 
 
@@ -96,6 +96,7 @@ def _load():
         "agf2_build_moments_noalloc": (I, [P, I, I, P, P, I, D, P, P, P]),
         "agf2_run_batched": (I, [P, I, ct.POINTER(agf2_system), ct.POINTER(agf2_opts), I,
                                  ct.POINTER(agf2_result), ct.POINTER(ct.c_int)]),
+        "agf2_spectral_function": (I, [P, P, P, I, I, P, I, D, P, P]),
     }
     for name, (res, args) in sig.items():
         fn = getattr(lib, name)
@@ -193,6 +194,11 @@ def agf2_run_batched(h, systems, opts=None, nworkers=0, allow=(AGF2_ERR_NO_CONVE
                                nworkers, out, st)
     _check(h, rc, allow)
     return rc, [out[i] for i in range(n)], [st[i] for i in range(n)]
+
+
+def agf2_spectral_function(h, e, C, nmo, nqmo, omega, nomega, eta, A_total, A_orb=None):
+    return _check(h, _lib.agf2_spectral_function(h, e, C, nmo, nqmo, omega, nomega, float(eta),
+                                                 A_total, A_orb))
 
 
 def agf2_get_state(h, e=None, C=None, D=None):

@@ -77,6 +77,11 @@ cudaError_t gm_energy(const double* V, const double* e, const double* E, int k, 
 cudaError_t shift_derivative(const double* S, const double* w, int k, int nv, double* out,
                              double* scratch, cudaStream_t s);
 cudaError_t set_identity(double* A, int n, double scale, cudaStream_t s);
+// lor[x][w] = eta/pi / ((w_j - e_x)^2 + eta^2);  out = a*a;  out[j] = sum_r M[r][j]
+cudaError_t lorentzian(const double* e, int nq, const double* w, int nw, double eta, double* lor,
+                       cudaStream_t s);
+cudaError_t square(const double* a, long long n, double* out, cudaStream_t s);
+cudaError_t column_sum(const double* M, int nrow, int ncol, double* out, cudaStream_t s);
 cudaError_t diag_from_vec(const double* d, int n, double* A, cudaStream_t s);
 // max |a - b| into *out (device)
 cudaError_t max_abs_diff(const double* a, const double* b, long long n, double* out, double* scratch,

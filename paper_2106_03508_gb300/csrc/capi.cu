@@ -1052,6 +1052,34 @@ int agf2_run(agf2_handle h, const double* hcore, const double* L, int naux, int 
   return rc != AGF2_OK ? rc : rc_conv;
 }
 
+int agf2_spectral_function(agf2_handle h, const double* e, const double* C, int nmo, int nqmo,
+                           const double* omega, int nomega, double eta, double* A_total,
+                           double* A_orb) {
+  return guarded(h, [&](agf2_context* ctx) {
+    if (nmo < 1 || nqmo < 1 || nomega < 1 || !(eta > 0.0))
+      fail(ctx, AGF2_ERR_INVALID_ARG, "need nmo, nqmo, nomega >= 1 and eta > 0");
+    check_dev_ptr(ctx, e, "e");
+    check_dev_ptr(ctx, C, "C");
+    check_dev_ptr(ctx, omega, "omega");
+    check_dev_ptr(ctx, A_total, "A_total");
+    if (A_orb) check_dev_ptr(ctx, A_orb, "A_orb");
+    cudaStream_t s = ctx->stream;
+    double* lor = ws(ctx, "sp_lor", (size_t)nqmo * nomega);
+    double* w2 = ws(ctx, "sp_w2", (size_t)nmo * nqmo);
+    double* orb = A_orb ? A_orb : ws(ctx, "sp_orb", (size_t)nmo * nomega);
+    CK(lorentzian(e, nqmo, omega, nomega, eta, lor, s));
+    CK(square(C, (long long)nmo * nqmo, w2, s));
+    DGemm g;  // A_orb[p][w] = sum_x C[p][x]^2 lor[x][w]
+    g.M = nmo; g.N = nomega; g.K = nqmo;
+    g.A = w2; g.sAm = nqmo; g.sAk = 1;
+    g.B = lor; g.sBk = nomega; g.sBn = 1;
+    g.C = orb; g.sCm = nomega; g.sCn = 1;
+    CK(dgemm(g, s));
+    CK(column_sum(orb, nmo, nomega, A_total, s));
+    sync(ctx);
+  });
+}
+
 int agf2_set_profiling(agf2_handle h, int enable) {
   return guarded(h, [&](agf2_context* ctx) {
     ctx->stats = KernelStats();

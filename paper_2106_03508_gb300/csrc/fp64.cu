@@ -318,6 +318,35 @@ __global__ void deriv_partial(const double* __restrict__ S, const double* __rest
   if (threadIdx.x == 0) part[blockIdx.x] = 4.0 * s;
 }
 
+// lor[x][w] = eta / pi / ((omega_w - e_x)^2 + eta^2)
+__global__ void lorentzian_kernel(const double* __restrict__ e, int nq, const double* __restrict__ w,
+                                  int nw, double eta, double* __restrict__ lor) {
+  const long long total = (long long)nq * nw;
+  const double c = eta / 3.14159265358979323846;
+  for (long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x; t < total;
+       t += (long long)gridDim.x * blockDim.x) {
+    const int x = (int)(t / nw), j = (int)(t % nw);
+    const double d = w[j] - e[x];
+    lor[t] = c / fma(d, d, eta * eta);
+  }
+}
+
+__global__ void square_kernel(const double* __restrict__ a, long long n, double* __restrict__ out) {
+  for (long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x; t < n;
+       t += (long long)gridDim.x * blockDim.x)
+    out[t] = a[t] * a[t];
+}
+
+// out[j] = sum_r M[r][j]  (column sums, one thread per column)
+__global__ void column_sum_kernel(const double* __restrict__ M, int nrow, int ncol,
+                                  double* __restrict__ out) {
+  const int j = blockIdx.x * blockDim.x + threadIdx.x;
+  if (j >= ncol) return;
+  double s = 0.0;
+  for (int r = 0; r < nrow; ++r) s += M[(long long)r * ncol + j];
+  out[j] = s;
+}
+
 __global__ void set_identity_kernel(double* A, int n, double scale) {
   const long long total = (long long)n * n;
   for (long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x; t < total;
@@ -482,6 +511,25 @@ cudaError_t shift_derivative(const double* S, const double* w, int k, int nv, do
   deriv_partial<<<RED_BLOCKS, RED_THREADS, 0, s>>>(S, w, k, nv, scratch);
   count_launch();
   final_sum<<<1, RED_THREADS, 0, s>>>(scratch, RED_BLOCKS, out);
+  count_launch();
+  return cudaGetLastError();
+}
+
+cudaError_t lorentzian(const double* e, int nq, const double* w, int nw, double eta, double* lor,
+                       cudaStream_t s) {
+  lorentzian_kernel<<<grid_for((long long)nq * nw), 256, 0, s>>>(e, nq, w, nw, eta, lor);
+  count_launch();
+  return cudaGetLastError();
+}
+
+cudaError_t square(const double* a, long long n, double* out, cudaStream_t s) {
+  square_kernel<<<grid_for(n), 256, 0, s>>>(a, n, out);
+  count_launch();
+  return cudaGetLastError();
+}
+
+cudaError_t column_sum(const double* M, int nrow, int ncol, double* out, cudaStream_t s) {
+  column_sum_kernel<<<(ncol + 255) / 256, 256, 0, s>>>(M, nrow, ncol, out);
   count_launch();
   return cudaGetLastError();
 }

@@ -265,3 +265,34 @@ def test_moment_elements_match_full_build():
         for n in range(2):
             assert abs(eh[t, n] - Uh[n, p, q]) <= 1e-12 * np.max(np.abs(Uh[n]))
             assert abs(ep[t, n] - Up[n, p, q]) <= 1e-12 * np.max(np.abs(Up[n]))
+
+
+def test_spectral_function_single_pole_and_hf():
+    """One pole of unit weight gives the Lorentzian eta/pi/((w-e)^2+eta^2);
+    at the HF reference (C = I) A_p is one Lorentzian at eps_p."""
+    w = np.linspace(-3, 3, 101)
+    A, Ao = O.spectral_function(np.array([0.4]), np.ones((1, 1)), w, 0.05)
+    assert np.allclose(A, 0.05 / np.pi / ((w - 0.4) ** 2 + 0.05 ** 2), rtol=1e-14)
+    eps = np.array([-1.0, 0.3, 2.0])
+    A, Ao = O.spectral_function(eps, np.eye(3), w, 0.1)
+    for p in range(3):
+        assert np.allclose(Ao[p], 0.1 / np.pi / ((w - eps[p]) ** 2 + 0.01), rtol=1e-14)
+
+
+def test_spectral_function_sum_rule():
+    """Completeness sum_x C_px^2 = 1 of the extended eigenvectors: each A_p
+    integrates to the closed-form Lorentzian mass inside the grid, and the
+    trace to N times ... summed the same way."""
+    rng = np.random.default_rng(4)
+    N = 5
+    F = rng.standard_normal((N, N)); F = F + F.T
+    e, C = O.diagonalise(F, rng.uniform(-3, 3, 2 * N), 0.5 * rng.standard_normal((N, 2 * N)))
+    eta, a, b = 0.05, -40.0, 40.0
+    w = np.linspace(a, b, 400001)
+    A, Ao = O.spectral_function(e, C, w, eta)
+    mass = (np.arctan((b - e) / eta) - np.arctan((a - e) / eta)) / np.pi   # per pole
+    expect = (C * C) @ mass
+    integ = np.trapezoid(Ao, w, axis=1)
+    assert np.allclose(integ, expect, atol=1e-6)
+    assert abs(np.trapezoid(A, w) - expect.sum()) < 1e-5
+    assert abs(expect.sum() - N) < 0.01
