@@ -76,7 +76,8 @@ int agf2_hcore_from_mo_energies(agf2_handle h, const double* L, int naux, int nm
  *   L      [naux][nmo][nmo]   in
  *   e      [nqmo]             in   pole energies; e < mu is occupied
  *   C      [nmo][nqmo]        in   physical-space couplings of the poles
- *   nmom   moment orders 0..nmom are produced (nmom >= 1)
+ *   nmom   moment orders 0..nmom are produced (nmom >= 1; AGF2_BF16X3
+ *          supports nmom <= 3, else AGF2_ERR_UNSUPPORTED)
  *   precision AGF2_FP64 or AGF2_BF16X3
  *   U_hole [nmom+1][nmo][nmo] out  (symmetrised)
  *   U_part [nmom+1][nmo][nmo] out  (symmetrised)
@@ -97,6 +98,26 @@ int agf2_build_moments(agf2_handle h, const double* L, int naux, int nmo,
  * Returns AGF2_ERR_NOT_PD if U^(0) is not positive definite.
  */
 int agf2_compress(agf2_handle h, const double* U, int nmo, double* E_aux, double* v_aux);
+
+/*
+ * Compression that conserves the moments U^(0..nmom), nmom = 2m+1 odd: the
+ * higher truncations of the compression paragraph (text before Eq.
+ * post_compression_h), as m+1 steps of the block Lanczos recursion that
+ * Eq. (block_lanczos_chol_3) starts, driven by the moments alone:
+ *   U^(0) = B0 B0^T;  A_i = Q_i^T E Q_i;
+ *   R_i = E Q_i - Q_i A_i - Q_{i-1} B_{i-1}^T,  R_i^T R_i = B_i^T B_i,
+ *   Q_{i+1} = R_i B_i^-1,
+ * with every Q_i^T E^s Q_j evaluated from U^(k+l+s).  The block-tridiagonal
+ * matrix (diagonal A_0..A_m, sub-diagonal B_1..B_m) = W diag(E) W^T gives
+ * the (m+1) nmo auxiliaries (E, B0 W[:nmo]); nmom = 1 is agf2_compress.
+ *   U     [nmom+1][nmo][nmo]        in   moments of one sector
+ *   E_aux [(nmom+1)/2 nmo]          out  ascending
+ *   v_aux [nmo][(nmom+1)/2 nmo]     out  column k couples auxiliary k
+ * Returns AGF2_ERR_NOT_PD if U^(0) or a Lanczos block R_i^T R_i is not
+ * positive definite, AGF2_ERR_INVALID_ARG if nmom is even.
+ */
+int agf2_compress_moments(agf2_handle h, const double* U, int nmo, int nmom, double* E_aux,
+                          double* v_aux);
 
 typedef struct {
     double tol_D;      /* convergence: max |D_new - D| (default 1e-10)        */
@@ -150,7 +171,9 @@ int agf2_fock_loop(agf2_handle h, const double* hcore, const double* L, int naux
 typedef struct {
     int    max_iter;   /* outer AGF2 iterations (default 50)                  */
     double conv_tol;   /* |dE_tot| convergence (default 1e-8 Ha)              */
-    int    nmom;       /* moment order (only 1 is supported: AGF2(1,0))       */
+    int    nmom;       /* conserved moments 0..nmom, odd: AGF2(m,0) with
+                          nmom = 2m+1 (default 1); (nmom+1)/2 nmo
+                          auxiliaries per sector; AGF2_BF16X3: nmom <= 3    */
     int    precision;  /* AGF2_FP64 or AGF2_BF16X3                            */
     double mix;        /* moment mixing U <- U_prev + mix (U - U_prev) (1.0)  */
     int    resume;     /* 1: continue from the state kept in the handle       */
@@ -174,7 +197,8 @@ void agf2_opts_default(agf2_opts* o);
 /*
  * Full AGF2 iteration from the Hartree-Fock reference in the MO basis (poles
  * e = eps0, C = I, D0 = aufbau density of nelec/2 orbitals): moments ->
- * moment mixing -> compression of each sector -> Fock loop -> energies,
+ * moment mixing -> compression of each sector (agf2_compress_moments) ->
+ * Fock loop over nmo + (nmom+1) nmo poles -> energies,
  * until |dE_tot| < conv_tol or max_iter.  E_1b = Tr[D(h+F)]/2; E_2b is the
  * Galitskii-Migdal sum over occupied poles x and particle-sector auxiliaries
  * k of (C_x . v_k)^2 / (e_x - E_k).  The final state (poles, self-energy,

@@ -220,6 +220,76 @@ def compress(U0: np.ndarray, U1: np.ndarray):
     return E, T @ W
 
 
+def compress_block_lanczos(U):
+    """Moment-conserving compression for nmom = 2m+1 (U has 2m+2 moments,
+    U[n] = v E^n v^T): m+1 steps of block Lanczos on the auxiliary space,
+    driven by the moments alone.  With Q_i = sum_k E^k V C[i][k] (V = v^T),
+    Q_i^T E^n Q_j = sum_kl C[i][k]^T U^(k+l+n) C[j][l]:
+      U0 = B0 B0^T (lower Cholesky), C[1][0] = B0^-T,
+      A_i = Q_i^T E Q_i,  R_i = E Q_i - Q_i A_i - Q_{i-1} B_{i-1}^T,
+      R_i^T R_i = B_i^T B_i (B_i upper),  Q_{i+1} = R_i B_i^-1.
+    The block-tridiagonal H = [[A_1, B_1^T], [B_1, A_2, ...]] of size (m+1) N
+    with couplings [B0, 0, ...] conserves U^(0..2m+1); diagonalised,
+    H = W diag(E') W^T, the auxiliaries are (E', B0 W[:N]).  m = 0 is
+    Eq. (block_lanczos_chol_3) with its M-block.  Returns (E' [(m+1)N],
+    v' [N, (m+1)N])."""
+    nmom = U.shape[0] - 1
+    if nmom % 2 != 1:
+        raise ValueError("nmom must be odd (2m+1)")
+    m = (nmom - 1) // 2
+    N = U.shape[1]
+    try:
+        B0 = np.linalg.cholesky(U[0])
+    except np.linalg.LinAlgError as exc:
+        raise NotPositiveDefinite(str(exc)) from exc
+
+    def mom(Ci, Cj, n):  # Q_i^T E^n Q_j
+        out = np.zeros((N, N))
+        for k, a in enumerate(Ci):
+            for l, b in enumerate(Cj):
+                out += a.T @ U[k + l + n] @ b
+        return out
+
+    C_prev = None
+    C_cur = [sla.solve_triangular(B0, np.eye(N), lower=True).T]   # B0^-T
+    A_blocks, B_blocks = [], []
+    B_prev = None
+    for i in range(m + 1):
+        A = mom(C_cur, C_cur, 1)
+        A = 0.5 * (A + A.T)
+        A_blocks.append(A)
+        if i == m:
+            break
+        # coefficients of R_i
+        CR = [np.zeros((N, N)) for _ in range(len(C_cur) + 1)]
+        for k, c in enumerate(C_cur):
+            CR[k + 1] += c
+            CR[k] -= c @ A
+        if C_prev is not None:
+            for k, c in enumerate(C_prev):
+                CR[k] -= c @ B_prev.T
+        S = mom(CR, CR, 0)
+        S = 0.5 * (S + S.T)
+        try:
+            Lc = np.linalg.cholesky(S)
+        except np.linalg.LinAlgError as exc:
+            raise NotPositiveDefinite(str(exc)) from exc
+        B = Lc.T                                      # B^T B = S
+        Binv = sla.solve_triangular(B, np.eye(N), lower=False)
+        C_prev, C_cur = C_cur, [c @ Binv for c in CR]
+        B_prev = B
+        B_blocks.append(B)
+    nb = m + 1
+    H = np.zeros((nb * N, nb * N))
+    for i in range(nb):
+        H[i * N:(i + 1) * N, i * N:(i + 1) * N] = A_blocks[i]
+    for i in range(m):
+        H[(i + 1) * N:(i + 2) * N, i * N:(i + 1) * N] = B_blocks[i]
+        H[i * N:(i + 1) * N, (i + 1) * N:(i + 2) * N] = B_blocks[i].T
+    E, W = np.linalg.eigh(H)
+    return E, B0 @ W[:N, :]
+
+
 # --------------------------------------------------------------------------
 # Extended Hamiltonian, Eq. (post_compression_h) / (dyson_eq_eig)
 # --------------------------------------------------------------------------
@@ -470,15 +540,20 @@ def run(h, L, nelec, eps0, max_iter=50, conv_tol=1e-8, nmom=1, fock_tol=1e-10,
             U = U_prev + mix * (U - U_prev)
         U_prev = U
         Uh, Up = U[: nmom + 1], U[nmom + 1:]
-        Eh, vh = compress(Uh[0], Uh[1])
-        Ep, vp = compress(Up[0], Up[1])
+        if nmom == 1:
+            Eh, vh = compress(Uh[0], Uh[1])
+            Ep, vp = compress(Up[0], Up[1])
+        else:
+            Eh, vh = compress_block_lanczos(Uh)
+            Ep, vp = compress_block_lanczos(Up)
         E_se = np.concatenate([Eh, Ep])
         v_se = np.concatenate([vh, vp], axis=1)
         fr = fock_loop(h, L, nelec, E_se, v_se, D, tol_D=fock_tol, max_cycle=fock_max_cycle)
         D, e, C, mu = fr.D, fr.e, fr.C, fr.mu
         k = fr.nocc_qmo
         E1 = energy_1body(h, fr.F, D)
-        E2 = energy_2body(e[:k], C[:, :k], fr.E_shift[N:], v_se[:, N:])
+        nh = len(Eh)
+        E2 = energy_2body(e[:k], C[:, :k], fr.E_shift[nh:], v_se[:, nh:])
         Et = E1 + E2
         rec = IterRecord(it, E1, E2, Et, -e[k - 1], -e[k], mu, fr.cycles)
         hist.append(rec)

@@ -46,11 +46,19 @@ cudaError_t sd_epilogue_fp64(const double* XIJ, const double* XJI, int nmo, int 
                              const double* e_in, bool diag, double* Y, double* Yw,
                              cudaStream_t s);
 
+// Z <- Z * w column-wise in the layout of sd_epilogue_fp64 (Y w^n -> Y w^(n+1)).
+cudaError_t weight_columns_fp64(double* Z, int nmo, int nI, int nJ, int n_in, const double* e_outI,
+                                const double* e_outJ, const double* e_in, cudaStream_t s);
+
 // Small FP64 kernels.
 cudaError_t gather_columns(const double* C, int nrow, int ncol_src, const int* idx, int n,
                            double* out, cudaStream_t s);                // out[r][t] = C[r][idx[t]]
 cudaError_t gather_vec(const double* e, const int* idx, int n, double* out, cudaStream_t s);
 cudaError_t symmetrize(double* U, int n, int nmat, cudaStream_t s);   // U <- (U+U^T)/2
+// dst (column-major, leading dimension ld) <- Lc^T, zero below the diagonal,
+// from a column-major lower Cholesky factor Lc [n x n]
+cudaError_t upper_from_lower_t(const double* Lc, int n, double* dst, long long ld,
+                               cudaStream_t s);
 cudaError_t axpby(double* y, const double* x, double a, double b, long long n, cudaStream_t s); // y = a*x + b*y
 cudaError_t build_extended_h(const double* F, const double* E, const double* v, double delta,
                              int nmo, int nse, double* H, cudaStream_t s);
@@ -90,10 +98,11 @@ cudaError_t add_scalar(double* x, double a, int n, cudaStream_t s);
 
 // Split-precision (BF16x3 / tcgen05) moment build from the FP64 rotated
 // tensors Lxo [o][N][naux], Lxv [v][N][naux], Lov [o][v][naux]; accumulates
-// into the zeroed U_hole, U_part [2][N][N] (not symmetrised).  Returns an
+// moments 0..nmom (nmom <= 3) into the zeroed U_hole, U_part [nmom+1][N][N]
+// (upper tiles mirrored, not symmetrised).  Returns an
 // AGF2 status; err receives a message.
 int mixed_build_moments_rotated(const double* Lxo, const double* Lxv, const double* Lov, int naux,
-                                int N, int o, int v, const double* eo, const double* ev,
+                                int N, int o, int v, const double* eo, const double* ev, int nmom,
                                 double* U_hole, double* U_part, std::string& err,
                                 cudaStream_t s, KernelStats* stats, void* workspace);
 // Workspace of the split-precision path, one per handle.

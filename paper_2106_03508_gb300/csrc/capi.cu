@@ -40,7 +40,7 @@ struct agf2_context {
   int* dev_info = nullptr;
   // ---- state kept between agf2_run calls ----
   bool have_state = false;
-  int nmo = 0, nq = 0;
+  int nmo = 0, nq = 0, nq_max = 0;  // nq_max: leading dimension of the state C
   double mu = 0.0, E_prev = 0.0, E_hf = 0.0;
   bool have_uprev = false;
   int iter = 0;
@@ -246,7 +246,7 @@ struct Sector {
   const double* e_in;
 };
 
-void sector_fp64(agf2_context* ctx, const Sector& S, int N, int naux, double* U0, double* U1) {
+void sector_fp64(agf2_context* ctx, const Sector& S, int N, int naux, int nmom, double* U) {
   cudaStream_t s = ctx->stream;
   const double budget_doubles = 2.0e8;  // 1.6 GB over the 6 block arrays
   int nb = (int)std::floor(std::sqrt(budget_doubles / 6.0 / ((double)N * S.n_in)));
@@ -276,12 +276,15 @@ void sector_fp64(agf2_context* ctx, const Sector& S, int N, int naux, double* U0
       if (!diag) pair_gemm(J0, nJ, I0, nI, XJI);
       CK(sd_epilogue_fp64(XIJ, XJI, N, nI, nJ, S.n_in, S.e_out + I0, S.e_out + J0, S.e_in, diag, Y,
                           Yw, s));
-      for (int n = 0; n < 2; ++n) {
-        DGemm g;  // U^(n) += Z Y^T, Z = Y (n = 0) or Yw (n = 1), K = 2 K1, split over K
+      for (int n = 0; n <= nmom; ++n) {
+        // U^(n) += Z Y^T, Z = Y w^n (Yw holds Y w^n for n >= 1), K = 2 K1, split over K
+        if (n >= 2)
+          CK(weight_columns_fp64(Yw, N, nI, nJ, S.n_in, S.e_out + I0, S.e_out + J0, S.e_in, s));
+        DGemm g;
         g.M = N; g.N = N; g.K = (int)(2 * K1);
         g.A = n == 0 ? Y : Yw; g.sAm = 2 * K1; g.sAk = 1;
         g.B = Y; g.sBk = 1; g.sBn = 2 * K1;
-        g.C = n == 0 ? U0 : U1; g.sCm = N; g.sCn = 1;
+        g.C = U + (long long)n * N * N; g.sCm = N; g.sCn = 1;
         g.atomic = true;
         const int tiles = ((N + 63) / 64) * ((N + 63) / 64);
         g.ksplit = std::max(1, std::min<int>((int)(2 * K1 / 256), (2 * 152 + tiles - 1) / tiles));
@@ -329,7 +332,6 @@ void build_moments_impl(agf2_context* ctx, const double* L, int naux, int N, con
   CK(gather_vec(e, idx, o, eo, s));
   CK(gather_vec(e, idx + o, v, ev, s));
   const long long NN = (long long)N * N;
-  const size_t mom_stride = (size_t)NN;
   CK(cudaMemsetAsync(Uh, 0, (nmom + 1) * NN * sizeof(double), s));
   CK(cudaMemsetAsync(Up, 0, (nmom + 1) * NN * sizeof(double), s));
   const long long NQ = (long long)N * naux;
@@ -358,14 +360,14 @@ void build_moments_impl(agf2_context* ctx, const double* L, int naux, int N, con
   }
   if (precision == AGF2_BF16X3) {
     if (!ctx->mixed_ws) ctx->mixed_ws = mixed_workspace_create();
-    int rc = mixed_build_moments_rotated(Lxo, Lxv, Lov, naux, N, o, v, eo, ev, Uh, Up, ctx->err, s,
-                                         &ctx->stats, ctx->mixed_ws);
+    int rc = mixed_build_moments_rotated(Lxo, Lxv, Lov, naux, N, o, v, eo, ev, nmom, Uh, Up,
+                                         ctx->err, s, &ctx->stats, ctx->mixed_ws);
     if (rc != AGF2_OK) throw Fail{rc};
   } else {
     Sector hole{o, v, Lxo, Lov, (long long)v * naux, (long long)naux, eo, ev};
     Sector part{v, o, Lxv, Lov, (long long)naux, (long long)v * naux, ev, eo};
-    sector_fp64(ctx, hole, N, naux, Uh, Uh + mom_stride);
-    sector_fp64(ctx, part, N, naux, Up, Up + mom_stride);
+    sector_fp64(ctx, hole, N, naux, nmom, Uh);
+    sector_fp64(ctx, part, N, naux, nmom, Up);
   }
   CK(symmetrize(Uh, N, nmom + 1, s));
   CK(symmetrize(Up, N, nmom + 1, s));
@@ -428,6 +430,126 @@ void compress_impl(agf2_context* ctx, const double* U, int n, double* E, double*
     CK(physical_block(W, n, n, n, tmp, s));
     CK(cudaMemcpy2DAsync(v_rowmajor, ldv * sizeof(double), tmp, n * sizeof(double),
                          n * sizeof(double), n, cudaMemcpyDeviceToDevice, s));
+  }
+  sync(ctx);
+}
+
+// Moment-conserving compression for nmom = 2m + 1 (the higher truncations of
+// the compression text before Eq. post_compression_h): m + 1 steps of
+// block Lanczos in the auxiliary space, driven by the moments U^(0..2m+1)
+// alone.  The Lanczos vectors are kept as coefficient lists, Q_i =
+// sum_k E^k V C_i[k] (V = v^T), so that Q_i^T E^s Q_j = sum_kl C_i[k]^T
+// U^(k+l+s) C_j[l]:
+//   U^(0) = B0 B0^T, C_0 = [B0^-T];  A_i = Q_i^T E Q_i;
+//   R_i = E Q_i - Q_i A_i - Q_{i-1} B_{i-1}^T,  R_i^T R_i = B_i^T B_i (B_i
+//   upper);  Q_{i+1} = R_i B_i^-1.
+// The block-tridiagonal H (diagonal A_i, sub-diagonal B_i) of order (m+1) N
+// is diagonalised, H = W diag(E) W^T, and the auxiliaries are
+// (E, B0 W[:N]), which conserve U^(0..2m+1).  m = 0 is compress_impl.
+// All matrices column-major; U^(n) symmetric, so its row-major array is its
+// own column-major view.  Output v row-major [n][(m+1) n] with row stride ldv.
+void compress_lanczos_impl(agf2_context* ctx, const double* U, int n, int nmom, double* E,
+                           double* v_rowmajor, long long ldv) {
+  const int m = (nmom - 1) / 2, nb = m + 1;
+  if (m == 0) {
+    compress_impl(ctx, U, n, E, v_rowmajor, ldv);
+    return;
+  }
+  Range rg("agf2_compress");
+  cudaStream_t s = ctx->stream;
+  const long long nn = (long long)n * n;
+  const int nh = nb * n;
+  auto Um = [&](int k) { return U + (long long)k * nn; };
+  double* B0 = ws(ctx, "lz_B0", nn);
+  double* tmp = ws(ctx, "lz_tmp", nn);
+  double* A = ws(ctx, "lz_A", nn);
+  double* S = ws(ctx, "lz_S", nn);
+  double* Bprev = ws(ctx, "lz_Bprev", nn);
+  double* Bcur = ws(ctx, "lz_Bcur", nn);
+  double* H = ws(ctx, "lz_H", (size_t)nh * nh);
+  double* pool[3] = {ws(ctx, "lz_pool0", (size_t)(nb + 1) * nn),
+                     ws(ctx, "lz_pool1", (size_t)(nb + 1) * nn),
+                     ws(ctx, "lz_pool2", (size_t)(nb + 1) * nn)};
+  const double one = 1.0, mone = -1.0, zero = 0.0;
+  auto potrf = [&](double* X, const char* what) {
+    int lwork = 0;
+    CKS(cusolverDnDpotrf_bufferSize(ctx->solver, CUBLAS_FILL_MODE_LOWER, n, X, n, &lwork));
+    double* work = ws(ctx, "potrf_work", (size_t)lwork);
+    CKS(cusolverDnDpotrf(ctx->solver, CUBLAS_FILL_MODE_LOWER, n, X, n, work, lwork,
+                         ctx->dev_info));
+    int info = 0;
+    CK(cudaMemcpyAsync(&info, ctx->dev_info, sizeof(int), cudaMemcpyDeviceToHost, s));
+    sync(ctx);
+    if (info != 0)
+      fail(ctx, AGF2_ERR_NOT_PD,
+           std::string(what) + " is not positive definite (potrf info " + std::to_string(info) +
+               ")");
+  };
+  auto mat = [&](double* base, int k) { return base + (long long)k * nn; };
+  // out = sum_kl Ci[k]^T U^(k+l+shift) Cj[l]
+  auto mom = [&](double* Ci, int ni, double* Cj, int nj, int shift, double* out) {
+    bool first = true;
+    for (int k = 0; k < ni; ++k)
+      for (int l = 0; l < nj; ++l) {
+        CKB(cublasDgemm(ctx->blas, CUBLAS_OP_N, CUBLAS_OP_N, n, n, n, &one, Um(k + l + shift), n,
+                        mat(Cj, l), n, &zero, tmp, n));
+        CKB(cublasDgemm(ctx->blas, CUBLAS_OP_T, CUBLAS_OP_N, n, n, n, &one, mat(Ci, k), n, tmp,
+                        n, first ? &zero : &one, out, n));
+        first = false;
+      }
+    CK(symmetrize(out, n, 1, s));
+  };
+  CK(cudaMemcpyAsync(B0, Um(0), nn * sizeof(double), cudaMemcpyDeviceToDevice, s));
+  potrf(B0, "U^(0)");
+  double *Ccur = pool[0], *Cprev = pool[1], *CR = pool[2];
+  int ncur = 1, nprev = 0;
+  CK(set_identity(Ccur, n, 1.0, s));  // C_0 = B0^-T: solve B0^T X = I
+  CKB(cublasDtrsm(ctx->blas, CUBLAS_SIDE_LEFT, CUBLAS_FILL_MODE_LOWER, CUBLAS_OP_T,
+                  CUBLAS_DIAG_NON_UNIT, n, n, &one, B0, n, Ccur, n));
+  CK(cudaMemsetAsync(H, 0, (size_t)nh * nh * sizeof(double), s));
+  for (int i = 0; i <= m; ++i) {
+    mom(Ccur, ncur, Ccur, ncur, 1, A);
+    CK(cudaMemcpy2DAsync(H + (long long)i * n + (long long)i * n * nh, nh * sizeof(double), A,
+                         n * sizeof(double), n * sizeof(double), n, cudaMemcpyDeviceToDevice, s));
+    if (i == m) break;
+    // R_i = E Q_i - Q_i A_i - Q_{i-1} B_{i-1}^T as coefficients CR[0..ncur]
+    CK(cudaMemsetAsync(CR, 0, (size_t)(ncur + 1) * nn * sizeof(double), s));
+    for (int k = 0; k < ncur; ++k) {
+      CKB(cublasDaxpy(ctx->blas, (int)nn, &one, mat(Ccur, k), 1, mat(CR, k + 1), 1));
+      CKB(cublasDgemm(ctx->blas, CUBLAS_OP_N, CUBLAS_OP_N, n, n, n, &mone, mat(Ccur, k), n, A, n,
+                      &one, mat(CR, k), n));
+    }
+    for (int k = 0; k < nprev; ++k)
+      CKB(cublasDgemm(ctx->blas, CUBLAS_OP_N, CUBLAS_OP_T, n, n, n, &mone, mat(Cprev, k), n,
+                      Bprev, n, &one, mat(CR, k), n));
+    mom(CR, ncur + 1, CR, ncur + 1, 0, S);
+    potrf(S, "R^T R of a Lanczos block");
+    CK(upper_from_lower_t(S, n, Bcur, n, s));
+    CK(upper_from_lower_t(S, n, H + (long long)(i + 1) * n + (long long)i * n * nh, nh, s));
+    // Q_{i+1} = R_i B_i^-1: solve X B_i = CR[k]
+    for (int k = 0; k <= ncur; ++k)
+      CKB(cublasDtrsm(ctx->blas, CUBLAS_SIDE_RIGHT, CUBLAS_FILL_MODE_UPPER, CUBLAS_OP_N,
+                      CUBLAS_DIAG_NON_UNIT, n, n, &one, Bcur, n, mat(CR, k), n));
+    std::swap(Bprev, Bcur);
+    double* old = Cprev;
+    Cprev = Ccur;
+    Ccur = CR;
+    CR = old;
+    nprev = ncur;
+    ncur += 1;
+  }
+  syevd(ctx, H, nh, E);
+  // v = B0 W[:n, :]
+  double* Vc = ws(ctx, "lz_V", (size_t)n * nh);
+  CKB(cublasDtrmm(ctx->blas, CUBLAS_SIDE_LEFT, CUBLAS_FILL_MODE_LOWER, CUBLAS_OP_N,
+                  CUBLAS_DIAG_NON_UNIT, n, nh, &one, B0, n, H, nh, Vc, n));
+  if (ldv == nh) {
+    CK(physical_block(Vc, n, n, nh, v_rowmajor, s));
+  } else {
+    double* vr = ws(ctx, "lz_vrm", (size_t)n * nh);
+    CK(physical_block(Vc, n, n, nh, vr, s));
+    CK(cudaMemcpy2DAsync(v_rowmajor, ldv * sizeof(double), vr, nh * sizeof(double),
+                         nh * sizeof(double), n, cudaMemcpyDeviceToDevice, s));
   }
   sync(ctx);
 }
@@ -879,9 +1001,10 @@ int agf2_build_moments(agf2_handle h, const double* L, int naux, int nmo, const 
   return guarded(h, [&](agf2_context* ctx) {
     if (naux < 1 || nmo < 1 || nqmo < 2 || nmom < 1)
       fail(ctx, AGF2_ERR_INVALID_ARG, "bad sizes");
-    if (nmom != 1) fail(ctx, AGF2_ERR_UNSUPPORTED, "only nmom = 1 (AGF2(1,0)) is implemented");
     if (precision != AGF2_FP64 && precision != AGF2_BF16X3)
       fail(ctx, AGF2_ERR_INVALID_ARG, "unknown precision");
+    if (precision == AGF2_BF16X3 && nmom > 3)
+      fail(ctx, AGF2_ERR_UNSUPPORTED, "AGF2_BF16X3 supports nmom <= 3");
     check_dev_ptr(ctx, L, "L");
     check_dev_ptr(ctx, e, "e");
     check_dev_ptr(ctx, C, "C");
@@ -898,6 +1021,18 @@ int agf2_compress(agf2_handle h, const double* U, int nmo, double* E_aux, double
     check_dev_ptr(ctx, E_aux, "E_aux");
     check_dev_ptr(ctx, v_aux, "v_aux");
     compress_impl(ctx, U, nmo, E_aux, v_aux, nmo);
+  });
+}
+
+int agf2_compress_moments(agf2_handle h, const double* U, int nmo, int nmom, double* E_aux,
+                          double* v_aux) {
+  return guarded(h, [&](agf2_context* ctx) {
+    if (nmo < 1) fail(ctx, AGF2_ERR_INVALID_ARG, "nmo < 1");
+    if (nmom < 1 || nmom % 2 == 0) fail(ctx, AGF2_ERR_INVALID_ARG, "nmom must be odd (2m+1)");
+    check_dev_ptr(ctx, U, "U");
+    check_dev_ptr(ctx, E_aux, "E_aux");
+    check_dev_ptr(ctx, v_aux, "v_aux");
+    compress_lanczos_impl(ctx, U, nmo, nmom, E_aux, v_aux, (long long)(nmom + 1) / 2 * nmo);
   });
 }
 
@@ -940,26 +1075,31 @@ int agf2_run(agf2_handle h, const double* hcore, const double* L, int naux, int 
     if (opts) o = *opts;
     if (naux < 1 || nmo < 2 || nelec < 2 || nelec % 2 || nelec >= 2 * nmo || o.max_iter < 1)
       fail(ctx, AGF2_ERR_INVALID_ARG, "bad sizes or options");
-    if (o.nmom != 1) fail(ctx, AGF2_ERR_UNSUPPORTED, "only nmom = 1 (AGF2(1,0)) is implemented");
+    if (o.nmom < 1 || o.nmom % 2 == 0)
+      fail(ctx, AGF2_ERR_INVALID_ARG, "nmom must be odd (AGF2(m,0) uses nmom = 2m+1)");
+    if (o.precision == AGF2_BF16X3 && o.nmom > 3)
+      fail(ctx, AGF2_ERR_UNSUPPORTED, "AGF2_BF16X3 supports nmom <= 3");
     check_dev_ptr(ctx, hcore, "hcore");
     check_dev_ptr(ctx, L, "L");
     cudaStream_t s = ctx->stream;
-    const int N = nmo, nse = 2 * nmo, nq_max = 3 * nmo;
+    const int nm = o.nmom + 1;          // moments per sector
+    const int nb = nm / 2;              // auxiliaries per sector = nb * nmo
+    const int N = nmo, nse = 2 * nb * nmo, nq_max = nmo + nse;
     const long long NN = (long long)N * N;
     double* e = ws(ctx, "st_e", nq_max);
     double* C = ws(ctx, "st_C", (size_t)N * nq_max);
     double* D = ws(ctx, "st_D", NN);
     double* F = ws(ctx, "st_F", NN);
-    double* U = ws(ctx, "st_U", 4 * NN);
-    double* Uprev = ws(ctx, "st_Uprev", 4 * NN);
+    double* U = ws(ctx, "st_U", 2 * nm * NN);
+    double* Uprev = ws(ctx, "st_Uprev", 2 * nm * NN);
     double* Ese = ws(ctx, "st_Ese", nse);
     double* vse = ws(ctx, "st_vse", (size_t)N * nse);
     double* eq = ws(ctx, "st_eq", nq_max);
     double* Cq = ws(ctx, "st_Cq", (size_t)N * nq_max);
     double* red = ws(ctx, "st_red", 1024);
-    double* V = ws(ctx, "st_V", (size_t)nq_max * N);
+    double* V = ws(ctx, "st_V", (size_t)nq_max * nb * N);
     const int nocc = nelec / 2;
-    if (!o.resume || !ctx->have_state || ctx->nmo != N) {
+    if (!o.resume || !ctx->have_state || ctx->nmo != N || ctx->nq_max != nq_max) {
       check_dev_ptr(ctx, eps0, "eps0");
       std::vector<double> e0 = to_host(ctx, eps0, N);
       CK(cudaMemcpyAsync(e, eps0, N * sizeof(double), cudaMemcpyDeviceToDevice, s));
@@ -978,6 +1118,7 @@ int agf2_run(agf2_handle h, const double* hcore, const double* L, int naux, int 
       ctx->mu = 0.5 * (e0[nocc - 1] + e0[nocc]);
       ctx->nq = N;
       ctx->nmo = N;
+      ctx->nq_max = nq_max;
       ctx->have_uprev = false;
       ctx->have_state = true;
       ctx->iter = 0;
@@ -993,15 +1134,17 @@ int agf2_run(agf2_handle h, const double* hcore, const double* L, int naux, int 
         out->flops_moments += (double)N * ps.o * ps.v * (double)(ps.o + ps.v) *
                               (2.0 * naux + 2.0 * (o.nmom + 1) * N);
       }
-      build_moments_impl(ctx, L, naux, N, e, C, ctx->nq, ctx->mu, 1, o.precision, U, U + 2 * NN);
+      build_moments_impl(ctx, L, naux, N, e, C, ctx->nq, ctx->mu, o.nmom, o.precision, U,
+                         U + nm * NN);
       out->t_moments += seconds_since(t0);
       t0 = std::chrono::steady_clock::now();
       ctx->iter += 1;
-      if (ctx->have_uprev) CK(axpby(U, Uprev, 1.0 - o.mix, o.mix, 4 * NN, s));
-      CK(cudaMemcpyAsync(Uprev, U, 4 * NN * sizeof(double), cudaMemcpyDeviceToDevice, s));
+      if (ctx->have_uprev) CK(axpby(U, Uprev, 1.0 - o.mix, o.mix, 2 * nm * NN, s));
+      CK(cudaMemcpyAsync(Uprev, U, 2 * nm * NN * sizeof(double), cudaMemcpyDeviceToDevice, s));
       ctx->have_uprev = true;
-      compress_impl(ctx, U, N, Ese, vse, nse);
-      compress_impl(ctx, U + 2 * NN, N, Ese + N, vse + N, nse);
+      // hole auxiliaries first, then particle ones, nb * N each
+      compress_lanczos_impl(ctx, U, N, o.nmom, Ese, vse, nse);
+      compress_lanczos_impl(ctx, U + nm * NN, N, o.nmom, Ese + nb * N, vse + nb * N, nse);
       out->t_compress += seconds_since(t0);
       t0 = std::chrono::steady_clock::now();
       FockOut fo = fock_loop_impl(ctx, hcore, L, naux, N, nelec, Ese, vse, nse, D, F, eq, Cq, o.fock);
@@ -1016,14 +1159,14 @@ int agf2_run(agf2_handle h, const double* hcore, const double* L, int naux, int 
       CK(dot(D, hcore, NN, red + 512, red, s));
       CK(dot(D, F, NN, red + 513, red, s));
       {
-        DGemm g;  // V[x][m] = sum_p C[p][x] v_>[p][m]
-        g.M = k; g.N = N; g.K = N;
+        DGemm g;  // V[x][m] = sum_p C[p][x] v_>[p][m], m over the nb N particle auxiliaries
+        g.M = k; g.N = nb * N; g.K = N;
         g.A = C; g.sAm = 1; g.sAk = nq_max;
-        g.B = vse + N; g.sBk = nse; g.sBn = 1;
-        g.C = V; g.sCm = N; g.sCn = 1;
+        g.B = vse + nb * N; g.sBk = nse; g.sBn = 1;
+        g.C = V; g.sCm = nb * N; g.sCn = 1;
         CK(dgemm(g, s));
       }
-      CK(gm_energy(V, e, Ese + N, k, N, red + 514, red, s));
+      CK(gm_energy(V, e, Ese + nb * N, k, nb * N, red + 514, red, s));
       std::vector<double> sc = to_host(ctx, red + 512, 3);
       std::vector<double> eh = to_host(ctx, e, nq_max);
       const double E1 = 0.5 * (sc[0] + sc[1]);
@@ -1156,13 +1299,13 @@ int agf2_run_batched(agf2_handle h, int nsys, const agf2_system* systems, const 
 int agf2_get_state(agf2_handle h, double* e, double* C, double* D, int* nqmo) {
   return guarded(h, [&](agf2_context* ctx) {
     if (!ctx->have_state) fail(ctx, AGF2_ERR_INVALID_ARG, "no state: call agf2_run first");
-    const int N = ctx->nmo, nq = ctx->nq, nq_max = 3 * N;
+    const int N = ctx->nmo, nq = ctx->nq, nq_max = ctx->nq_max;
     cudaStream_t s = ctx->stream;
     if (nqmo) *nqmo = nq;
     if (e) CK(cudaMemcpyAsync(e, ws(ctx, "st_e", nq_max), nq * sizeof(double),
                               cudaMemcpyDeviceToDevice, s));
     if (C) {
-      // state C has leading dimension 3N once iterations ran, N before
+      // state C has leading dimension nq_max once iterations ran, N before
       const int ld = (nq == N) ? N : nq_max;
       CK(cudaMemcpy2DAsync(C, nq * sizeof(double), ws(ctx, "st_C", (size_t)N * nq_max),
                            ld * sizeof(double), nq * sizeof(double), N, cudaMemcpyDeviceToDevice, s));

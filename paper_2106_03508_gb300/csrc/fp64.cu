@@ -108,6 +108,24 @@ __global__ void sd_epilogue_kernel(const double* __restrict__ XIJ, const double*
   }
 }
 
+// Z[p][k] *= (e_out[x] + e_out[y] - e_in[c]) for the [S | D] layout of the
+// FP64 epilogue (k mod K1 = (ii*nJ + jj)*n_in + c); turns Y w^n into Y w^(n+1).
+__global__ void weight_columns_kernel(double* __restrict__ Z, int nmo, int nI, int nJ, int n_in,
+                                      const double* __restrict__ eI, const double* __restrict__ eJ,
+                                      const double* __restrict__ ein) {
+  const long long K1 = (long long)nI * nJ * n_in;
+  const long long total = (long long)nmo * 2 * K1;
+  for (long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x; t < total;
+       t += (long long)gridDim.x * blockDim.x) {
+    const long long k = t % (2 * K1);
+    const long long k1 = k % K1;
+    const int ii = (int)(k1 / ((long long)nJ * n_in));
+    const int rem = (int)(k1 - (long long)ii * nJ * n_in);
+    const int jj = rem / n_in, c = rem - jj * n_in;
+    Z[t] *= eI[ii] + eJ[jj] - ein[c];
+  }
+}
+
 inline int grid_for(long long n, int bs = 256) {
   long long g = (n + bs - 1) / bs;
   if (g > 152LL * 64) g = 152LL * 64;
@@ -410,6 +428,14 @@ cudaError_t sd_epilogue_fp64(const double* XIJ, const double* XJI, int nmo, int 
   return cudaGetLastError();
 }
 
+cudaError_t weight_columns_fp64(double* Z, int nmo, int nI, int nJ, int n_in, const double* e_outI,
+                                const double* e_outJ, const double* e_in, cudaStream_t s) {
+  const long long total = (long long)nmo * 2 * nI * nJ * n_in;
+  weight_columns_kernel<<<grid_for(total), 256, 0, s>>>(Z, nmo, nI, nJ, n_in, e_outI, e_outJ, e_in);
+  count_launch();
+  return cudaGetLastError();
+}
+
 cudaError_t gather_columns(const double* C, int nrow, int ncol_src, const int* idx, int n,
                            double* out, cudaStream_t s) {
   if (n <= 0) return cudaSuccess;
@@ -447,6 +473,25 @@ cudaError_t build_extended_h(const double* F, const double* E, const double* v, 
 
 cudaError_t column_weights(const double* V, int ld, int nmo, int ncol, double* w, cudaStream_t s) {
   column_weights_kernel<<<(ncol * 32 + 255) / 256, 256, 0, s>>>(V, ld, nmo, ncol, w);
+  count_launch();
+  return cudaGetLastError();
+}
+
+// dst[r + c ld] = Lc(c, r) for r <= c, 0 below: the explicit upper factor
+// B = Lc^T of a column-major lower Cholesky factor (upper part of Lc ignored).
+__global__ void upper_from_lower_t_kernel(const double* __restrict__ Lc, int n,
+                                          double* __restrict__ dst, long long ld) {
+  const long long total = (long long)n * n;
+  for (long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x; t < total;
+       t += (long long)gridDim.x * blockDim.x) {
+    const int c = (int)(t / n), r = (int)(t % n);
+    dst[r + c * ld] = (r <= c) ? Lc[c + (long long)r * n] : 0.0;
+  }
+}
+
+cudaError_t upper_from_lower_t(const double* Lc, int n, double* dst, long long ld,
+                               cudaStream_t s) {
+  upper_from_lower_t_kernel<<<grid_for((long long)n * n), 256, 0, s>>>(Lc, n, dst, ld);
   count_launch();
   return cudaGetLastError();
 }

@@ -77,16 +77,15 @@ struct Params {
   const int2* pairs;
   const double* e_out;
   const double* e_in;
-  const float* unitA;   // MODE_PAIR: slicing unit of Lx rows [x][p]; MOMENT: of Y or Yw rows
-  const float* unitA2;  // MOMENT: unit of Yw rows
+  const float* unitA;   // MODE_PAIR: slicing unit of Lx rows [x][p]; MOMENT: [nm][N] of Y w^n rows
   const float* unitB;   // MODE_PAIR: unit of Lov rows [i][a];        MOMENT: of Y rows
+  int nm;               // MODE_MOMENT: moments computed (nmom + 1)
   int v_stride;         // MODE_PAIR: v (row index of Lov rows is i * v + a)
   float* X;            // MODE_PAIR output: FP32 X_xy [N][np][2][ncp] (row stride Ks)
   int ncp;             // MODE_PAIR: n_cchunks * BN (padded inner count)
   long long Ks;
   long long plane;     // N * Ks
-  double* U0;
-  double* U1;
+  double* U0;          // MODE_MOMENT: [nm][N][N]
   int* err;
 };
 
@@ -95,15 +94,15 @@ struct Segment {
   int b_row, b_idx;   // B tile
   int acc_col;        // accumulator column offset
   int kbeg, kend;     // K steps
-  bool a_w;           // MODE_MOMENT: A from the Yw map
+  int a_plane;        // MODE_MOMENT: moment n (A rows are Y w^n)
 };
 
 __device__ __forceinline__ void load_a(const CUtensorMap* mapA, uint8_t* dst, uint64_t* bar,
                                        const Params& P, const Segment& s, int ks, int limb) {
   if (P.n_out > 0)  // MODE_PAIR: A map dims (Qs, N, 3*n_out)
     tc::tma_load_3d(dst, mapA, bar, ks * BK, s.a_row, limb * P.n_out + s.a_idx);
-  else              // MODE_MOMENT: Y/Yw map dims (K, N, 3)
-    tc::tma_load_3d(dst, mapA, bar, ks * BK, s.a_row, limb);
+  else              // MODE_MOMENT: map over [nm][3] planes of Y w^n, dims (K, N, 3 nm)
+    tc::tma_load_3d(dst, mapA, bar, ks * BK, s.a_row, s.a_plane * 3 + limb);
 }
 
 // Work of one tile: one K segment into one accumulator set (nseg = 0: no
@@ -132,13 +131,13 @@ __device__ __forceinline__ TileWork decode_tile(const Params& P, int t) {
     w.p0 = pt * BM;
     w.c0 = cc * BN;
     const int xa = w.orient ? w.pr.y : w.pr.x, yb = w.orient ? w.pr.x : w.pr.y;
-    w.seg[0] = Segment{w.p0, xa, w.c0, yb, 0, 0, P.ksteps, false};
+    w.seg[0] = Segment{w.p0, xa, w.c0, yb, 0, 0, P.ksteps, 0};
     if (w.orient && w.pr.x == w.pr.y) w.nseg = 0;  // X_yx == X_xy on the diagonal
   } else {
     // U is symmetric: only tiles with qt >= pt (upper triangle of tiles)
     int b = t;
     const int sp = b % P.nsplit; b /= P.nsplit;
-    w.moment = b % 2; b /= 2;
+    w.moment = b % P.nm; b /= P.nm;
     int pt = 0, qt = 0;
     for (int r = 0, left = b; r < P.n_ptiles; ++r) {
       const int row = P.n_ptiles - r;  // tiles qt = r .. n_ptiles - 1
@@ -149,7 +148,7 @@ __device__ __forceinline__ TileWork decode_tile(const Params& P, int t) {
     w.q0 = qt * BN;
     const int kb = sp * P.ksplit;
     const int ke = min(P.ksteps, kb + P.ksplit);
-    w.seg[0] = Segment{w.p0, 0, w.q0, 0, 0, kb, ke, w.moment == 1};
+    w.seg[0] = Segment{w.p0, 0, w.q0, 0, 0, kb, ke, w.moment};
   }
   return w;
 }
@@ -164,8 +163,8 @@ __device__ __forceinline__ TileWork decode_tile(const Params& P, int t) {
 // overlaps the next tile's MMAs.
 template <int MODE>
 __global__ void __launch_bounds__(NTHREADS, 1)
-gemm6_kernel(const __grid_constant__ CUtensorMap mapA, const __grid_constant__ CUtensorMap mapA2,
-             const __grid_constant__ CUtensorMap mapB, const Params P) {
+gemm6_kernel(const __grid_constant__ CUtensorMap mapA, const __grid_constant__ CUtensorMap mapB,
+             const Params P) {
   constexpr int NBUF = 2;
   constexpr int BUF_COLS = 2 * BN;
   constexpr int N_EPI_WARPS = (NTHREADS / 32) - 2;
@@ -211,7 +210,6 @@ gemm6_kernel(const __grid_constant__ CUtensorMap mapA, const __grid_constant__ C
     // ---------------- TMA producer ----------------
     tc::tma_prefetch(&mapA);
     tc::tma_prefetch(&mapB);
-    if (MODE == MODE_MOMENT) tc::tma_prefetch(&mapA2);
     int t = 0;
     bool ok = true;
     for (int tile = blockIdx.x; tile < P.ntiles && ok; tile += gridDim.x) {
@@ -234,7 +232,7 @@ gemm6_kernel(const __grid_constant__ CUtensorMap mapA, const __grid_constant__ C
                 tc::tma_load_4d(base + 3 * TILE_A + l * TILE_B, &mapB, &full_bar[st], ks * BK,
                                 s.b_idx, s.b_row, l);
             } else {
-              load_a(s.a_w ? &mapA2 : &mapA, base + l * TILE_A, &full_bar[st], P, s, ks, l);
+              load_a(&mapA, base + l * TILE_A, &full_bar[st], P, s, ks, l);
               tc::tma_load_3d(base + 3 * TILE_A + l * TILE_B, &mapB, &full_bar[st], ks * BK,
                               s.b_row, l);
             }
@@ -339,8 +337,8 @@ gemm6_kernel(const __grid_constant__ CUtensorMap mapA, const __grid_constant__ C
         }
 
       } else {
-        double* U = w.moment == 0 ? P.U0 : P.U1;
-        const double uA = (p < P.N) ? (double)(w.moment == 0 ? P.unitA : P.unitA2)[p] : 0.0;
+        double* U = P.U0 + (long long)w.moment * P.N * P.N;
+        const double uA = (p < P.N) ? (double)P.unitA[(long long)w.moment * P.N + p] : 0.0;
         for (int cb = col0; cb < col0 + BN / 2; cb += 16) {
           float hi[16], lo[16];
           tc::tmem_ld16(trow + cb, hi);
@@ -444,19 +442,19 @@ __global__ void slice_rows_kernel(const T* __restrict__ src, long long nrow, int
 // from a bound (e.g. sqrt(6) max|X|) coarsens the grid and the squared
 // rounding error biases diag U^(0) (measured +1e-8 relative).  Four
 // consecutive c per thread; grid = (blocks over pair x inner / 4, N rows).
+constexpr int MAXM = 4;  // moments 0..3 on the split-precision path
+
 struct Combine {
   const float* X;
   long long xrow;  // row stride of X
-  int np, ncp, n_in, N, kpp, pair0;
+  int np, ncp, n_in, N, kpp, pair0, nm;
   const int2* pairs;
   const double* e_out;
   const double* e_in;
-  unsigned* maxbits;  // [2][N]: |Y|, |Yw|
-  __nv_bfloat16* Y;
-  __nv_bfloat16* Yw;
-  long long Ks, plane;
-  float* unitY;
-  float* unitYw;
+  unsigned* maxbits;   // [nm][N]: max |Y w^n| per row
+  __nv_bfloat16* Y;    // [nm][3][N][Ks] limb planes of Y w^n
+  long long Ks, plane; // plane = N Ks
+  float* unit;         // [nm][N]
 };
 
 __device__ __forceinline__ void store4(__nv_bfloat16* base, long long plane, long long k,
@@ -477,16 +475,15 @@ __global__ void __launch_bounds__(256) combine_kernel(const Combine C) {
   const int p = blockIdx.y;
   const int nq = C.ncp / 4;  // groups of 4 inner poles per pair
   const int total = C.np * nq;
-  float uy = 1.f, uyw = 1.f;
-  if (PASS == 1) {
-    uy = tc::slice_unitf(__uint_as_float(C.maxbits[p]));
-    uyw = tc::slice_unitf(__uint_as_float(C.maxbits[C.N + p]));
+  float iu[MAXM], mx[MAXM];
+#pragma unroll
+  for (int n = 0; n < MAXM; ++n) {
+    iu[n] = 1.f;
+    mx[n] = 0.f;
+    if (PASS == 1 && n < C.nm)
+      iu[n] = 1.0f / tc::slice_unitf(__uint_as_float(C.maxbits[(long long)n * C.N + p]));
   }
-  const float iuy = 1.0f / uy, iuyw = 1.0f / uyw;
-  float my = 0.f, mw = 0.f;
   const float* xr = C.X + (long long)p * C.xrow;
-  __nv_bfloat16* yr = C.Y + (long long)p * C.Ks;
-  __nv_bfloat16* ywr = C.Yw + (long long)p * C.Ks;
   for (int e = blockIdx.x * blockDim.x + threadIdx.x; e < total; e += gridDim.x * blockDim.x) {
     const int pl = e / nq, c0 = (e - pl * nq) * 4;
     const int2 pr = C.pairs[C.pair0 + pl];
@@ -514,45 +511,50 @@ __global__ void __launch_bounds__(256) combine_kernel(const Combine C) {
         wt[j] = (float)(ex - C.e_in[c]);
       }
     }
-    if (PASS == 0) {
+    const long long k = (long long)pl * C.kpp + (c0 / BN) * KCHUNK + (c0 % BN);
+#pragma unroll
+    for (int n = 0; n < MAXM; ++n) {
+      if (n >= C.nm) break;
+      if (PASS == 0) {
+#pragma unroll
+        for (int j = 0; j < 4; ++j) mx[n] = fmaxf(mx[n], fmaxf(fabsf(ys[j]), fabsf(yd[j])));
+      } else {
+        __nv_bfloat16 hs[3][4], hd[3][4];
+#pragma unroll
+        for (int j = 0; j < 4; ++j) {
+          tc::slice3f(ys[j] * iu[n], hs[0][j], hs[1][j], hs[2][j]);
+          tc::slice3f(yd[j] * iu[n], hd[0][j], hd[1][j], hd[2][j]);
+        }
+        __nv_bfloat16* base = C.Y + (long long)n * 3 * C.plane + (long long)p * C.Ks;
+        store4(base, C.plane, k, hs);
+        store4(base, C.plane, k + BN, hd);
+      }
+      // next power: Y w^(n+1)
 #pragma unroll
       for (int j = 0; j < 4; ++j) {
-        my = fmaxf(my, fmaxf(fabsf(ys[j]), fabsf(yd[j])));
-        mw = fmaxf(mw, fmaxf(fabsf(ys[j] * wt[j]), fabsf(yd[j] * wt[j])));
+        ys[j] *= wt[j];
+        yd[j] *= wt[j];
       }
-    } else {
-      __nv_bfloat16 hs[3][4], hd[3][4], ws[3][4], wd[3][4];
-#pragma unroll
-      for (int j = 0; j < 4; ++j) {
-        tc::slice3f(ys[j] * iuy, hs[0][j], hs[1][j], hs[2][j]);
-        tc::slice3f(yd[j] * iuy, hd[0][j], hd[1][j], hd[2][j]);
-        tc::slice3f(ys[j] * wt[j] * iuyw, ws[0][j], ws[1][j], ws[2][j]);
-        tc::slice3f(yd[j] * wt[j] * iuyw, wd[0][j], wd[1][j], wd[2][j]);
-      }
-      const long long k = (long long)pl * C.kpp + (c0 / BN) * KCHUNK + (c0 % BN);
-      store4(yr, C.plane, k, hs);
-      store4(yr, C.plane, k + BN, hd);
-      store4(ywr, C.plane, k, ws);
-      store4(ywr, C.plane, k + BN, wd);
     }
   }
   if (PASS == 0) {
-    __shared__ float shy[8], shw[8];
+    __shared__ float sh[MAXM][8];
 #pragma unroll
-    for (int o = 16; o > 0; o >>= 1) {
-      my = fmaxf(my, __shfl_xor_sync(0xffffffffu, my, o));
-      mw = fmaxf(mw, __shfl_xor_sync(0xffffffffu, mw, o));
+    for (int n = 0; n < MAXM; ++n) {
+      float m = mx[n];
+#pragma unroll
+      for (int o = 16; o > 0; o >>= 1) m = fmaxf(m, __shfl_xor_sync(0xffffffffu, m, o));
+      if ((threadIdx.x & 31) == 0) sh[n][threadIdx.x >> 5] = m;
     }
-    if ((threadIdx.x & 31) == 0) { shy[threadIdx.x >> 5] = my; shw[threadIdx.x >> 5] = mw; }
     __syncthreads();
-    if (threadIdx.x == 0) {
-      for (int w = 1; w < (int)(blockDim.x >> 5); ++w) { my = fmaxf(my, shy[w]); mw = fmaxf(mw, shw[w]); }
-      atomicMax(C.maxbits + p, __float_as_uint(my));
-      atomicMax(C.maxbits + C.N + p, __float_as_uint(mw));
+    if (threadIdx.x < C.nm) {
+      float m = 0.f;
+      for (int w = 0; w < (int)(blockDim.x >> 5); ++w) m = fmaxf(m, sh[threadIdx.x][w]);
+      atomicMax(C.maxbits + (long long)threadIdx.x * C.N + p, __float_as_uint(m));
     }
-  } else if (blockIdx.x == 0 && threadIdx.x == 0) {
-    C.unitY[p] = uy;
-    C.unitYw[p] = uyw;
+  } else if (blockIdx.x == 0 && threadIdx.x < C.nm) {
+    C.unit[(long long)threadIdx.x * C.N + p] =
+        tc::slice_unitf(__uint_as_float(C.maxbits[(long long)threadIdx.x * C.N + p]));
   }
 }
 
@@ -608,8 +610,8 @@ struct Buffers {
 };
 
 struct MixedWs {
-  Buffers lx_o, lx_v, l_ov, y, yw, pairs, err;
-  Buffers u_xo, u_xv, u_ov, u_y, u_yw, y32, yw32, maxbits;
+  Buffers lx_o, lx_v, l_ov, y, pairs, err;
+  Buffers u_xo, u_xv, u_ov, u_y, x32, maxbits;
 };
 
 std::mutex g_attr_mu;
@@ -640,14 +642,14 @@ void* mixed_workspace_create() { return new MixedWs(); }
 void mixed_workspace_destroy(void* w) {
   if (!w) return;
   MixedWs* W = static_cast<MixedWs*>(w);
-  for (Buffers* b : {&W->lx_o, &W->lx_v, &W->l_ov, &W->y, &W->yw, &W->pairs, &W->err, &W->u_xo,
-                     &W->u_xv, &W->u_ov, &W->u_y, &W->u_yw, &W->y32, &W->yw32, &W->maxbits})
+  for (Buffers* b : {&W->lx_o, &W->lx_v, &W->l_ov, &W->y, &W->pairs, &W->err, &W->u_xo,
+                     &W->u_xv, &W->u_ov, &W->u_y, &W->x32, &W->maxbits})
     if (b->p) cudaFree(b->p);
   delete W;
 }
 
 int mixed_build_moments_rotated(const double* Lxo, const double* Lxv, const double* Lov, int naux,
-                                int N, int o, int v, const double* eo, const double* ev,
+                                int N, int o, int v, const double* eo, const double* ev, int nmom,
                                 double* U_hole, double* U_part, std::string& err,
                                 cudaStream_t s, KernelStats* stats, void* workspace) {
   // CUDA events around the tcgen05 launches when stats->enabled
@@ -672,6 +674,10 @@ int mixed_build_moments_rotated(const double* Lxo, const double* Lxv, const doub
   int dev = 0;
   cudaGetDevice(&dev);
   MixedWs& W = *static_cast<MixedWs*>(workspace);
+  if (nmom < 1 || nmom + 1 > MAXM) {
+    err = "the split-precision moment build supports nmom = 1..3";
+    return AGF2_ERR_UNSUPPORTED;
+  }
   {
     std::lock_guard<std::mutex> attr_lock(g_attr_mu);
     if (!g_attr_done[dev & 63]) {
@@ -698,9 +704,9 @@ int mixed_build_moments_rotated(const double* Lxo, const double* Lxv, const doub
   float* u_xo = grow<float>(W.u_xo, (size_t)o * N, err);
   float* u_xv = grow<float>(W.u_xv, (size_t)v * N, err);
   float* u_ov = grow<float>(W.u_ov, (size_t)o * v, err);
-  float* u_y = grow<float>(W.u_y, N, err);
-  float* u_yw = grow<float>(W.u_yw, N, err);
-  if (!u_xo || !u_xv || !u_ov || !u_y || !u_yw) return AGF2_ERR_OOM;
+  const int nm = nmom + 1;
+  float* u_y = grow<float>(W.u_y, (size_t)nm * N, err);
+  if (!u_xo || !u_xv || !u_ov || !u_y) return AGF2_ERR_OOM;
   // rotated FP64 tensors have layout [x][p][Q] / [j][a][Q] with row length naux
   auto slice = [&](auto* src, long long rows, int ncol, long long ld, int ncolp,
                    __nv_bfloat16* dst, float* unit) {
@@ -758,7 +764,7 @@ int mixed_build_moments_rotated(const double* Lxo, const double* Lxv, const doub
     // pairs per block: large enough that GEMM 2's split-K tiles are long (each
     // tile ends in a 128x128 FP64 drain), about 256 MB of X + Y + Yw, and a
     // whole number of waves of the persistent CTAs
-    const double per_pair = (double)N * (kpp * 2 /*Y,Yw*/ * 3 /*limbs*/ * 2 /*bytes*/ +
+    const double per_pair = (double)N * (kpp * nm /*Y w^n*/ * 3 /*limbs*/ * 2 /*bytes*/ +
                                          2.0 * ncp * 4 /*X, both orders*/);
     const int tpp = 2 * n_ptiles * n_cchunks;  // tiles per unordered pair
     int bp = (int)std::max(1.0, std::floor(256.0e6 / per_pair));
@@ -772,11 +778,10 @@ int mixed_build_moments_rotated(const double* Lxo, const double* Lxv, const doub
     bp = std::max(1, std::min<int>(bp, (int)pairs.size()));
     const long long Ks = (long long)bp * kpp;
     const long long Kx = (long long)bp * 2 * ncp;  // row length of X
-    __nv_bfloat16* y = grow<__nv_bfloat16>(W.y, 3LL * N * Ks, err);
-    __nv_bfloat16* yw = grow<__nv_bfloat16>(W.yw, 3LL * N * Ks, err);
-    float* x32 = grow<float>(W.y32, (size_t)N * Kx, err);
-    unsigned* maxbits = grow<unsigned>(W.maxbits, 2 * (size_t)N, err);
-    if (!y || !yw || !x32 || !maxbits) return AGF2_ERR_OOM;
+    __nv_bfloat16* y = grow<__nv_bfloat16>(W.y, 3LL * nm * N * Ks, err);  // [nm][3][N][Ks]
+    float* x32 = grow<float>(W.x32, (size_t)N * Kx, err);
+    unsigned* maxbits = grow<unsigned>(W.maxbits, (size_t)nm * N, err);
+    if (!y || !x32 || !maxbits) return AGF2_ERR_OOM;
     for (size_t b0 = 0; b0 < pairs.size(); b0 += bp) {
       const int np = (int)std::min<size_t>(bp, pairs.size() - b0);
       const long long K = (long long)np * kpp;
@@ -807,13 +812,13 @@ int mixed_build_moments_rotated(const double* Lxo, const double* Lxv, const doub
       for (int t = 0; t < np; ++t) ordered += (pairs[b0 + t].x == pairs[b0 + t].y) ? 1 : 2;
       mark(0, 2.0 * N * (double)naux * n_in * (double)ordered);
       gemm6_kernel<MODE_PAIR><<<grid1, NTHREADS, SMEM_BYTES, s>>>(
-          hole ? map_xo : map_xv, hole ? map_xo : map_xv, hole ? map_b_hole : map_b_part, P);
+          hole ? map_xo : map_xv, hole ? map_b_hole : map_b_part, P);
       mark_end();
       count_launch();
       // S/D and energy weights, then fixed-point limbs with each row's exact unit
-      Combine C{x32, Kx, np, ncp, n_in, N, (int)kpp, (int)b0, dpairs, e_out, e_in, maxbits,
-                y, yw, Ks, (long long)N * Ks, u_y, u_yw};
-      cudaMemsetAsync(maxbits, 0, 2 * N * sizeof(unsigned), s);
+      Combine C{x32, Kx, np, ncp, n_in, N, (int)kpp, (int)b0, nm, dpairs, e_out, e_in, maxbits,
+                y, Ks, (long long)N * Ks, u_y};
+      cudaMemsetAsync(maxbits, 0, (size_t)nm * N * sizeof(unsigned), s);
       const long long per_row = (long long)np * ncp / 4;
       const dim3 gc((unsigned)std::max(1LL, std::min<long long>((per_row + 1023) / 1024, 64)),
                     (unsigned)N);
@@ -821,18 +826,18 @@ int mixed_build_moments_rotated(const double* Lxo, const double* Lxv, const doub
       combine_kernel<1><<<gc, 256, 0, s>>>(C);
       count_launch(2);
       // GEMM 2 over this block's K = np * kpp
-      CUtensorMap map_y, map_yw;
-      cuuint64_t dims[3] = {(cuuint64_t)K, (cuuint64_t)N, 3};
+      CUtensorMap map_y;  // all [nm][3] planes; plane index = moment * 3 + limb
+      cuuint64_t dims[3] = {(cuuint64_t)K, (cuuint64_t)N, (cuuint64_t)3 * nm};
       cuuint64_t str[2] = {(cuuint64_t)Ks * 2, (cuuint64_t)N * Ks * 2};
       cuuint32_t box[3] = {BK, BM, 1};
       if (!make_map(&map_y, y, 3, dims, str, box, err)) return AGF2_ERR_CUDA;
-      if (!make_map(&map_yw, yw, 3, dims, str, box, err)) return AGF2_ERR_CUDA;
       Params M{};
       M.N = N;
       M.n_ptiles = n_ptiles;
       M.n_qtiles = (N + BN - 1) / BN;
       M.ksteps = (int)((K + BK - 1) / BK);
-      const int tiles = M.n_ptiles * (M.n_ptiles + 1) / 2 * 2;  // upper tiles x 2 moments
+      M.nm = nm;
+      const int tiles = M.n_ptiles * (M.n_ptiles + 1) / 2 * nm;  // upper tiles x moments
       // about two tiles per persistent CTA, so each drain overlaps the next tile's MMAs
       int nsplit = std::max(1, (nsm * 2 + tiles - 1) / tiles);
       nsplit = std::min(nsplit, M.ksteps);
@@ -841,15 +846,13 @@ int mixed_build_moments_rotated(const double* Lxo, const double* Lxv, const doub
       M.ntiles = tiles * M.nsplit;
       M.n_out = 0;
       M.unitA = u_y;
-      M.unitA2 = u_yw;
       M.unitB = u_y;
       M.U0 = U;
-      M.U1 = U + (long long)N * N;
       M.err = derr;
-      // algorithmic flops: both moments over the ordered pairs, 2 N^2 per (pair, c)
-      mark(1, 2.0 * 2.0 * (double)N * N * (double)n_in * (double)ordered);
-      gemm6_kernel<MODE_MOMENT><<<std::min(M.ntiles, nsm), NTHREADS, SMEM_BYTES, s>>>(
-          map_y, map_yw, map_y, M);
+      // algorithmic flops: every moment over the ordered pairs, 2 N^2 per (pair, c)
+      mark(1, 2.0 * nm * (double)N * N * (double)n_in * (double)ordered);
+      gemm6_kernel<MODE_MOMENT><<<std::min(M.ntiles, nsm), NTHREADS, SMEM_BYTES, s>>>(map_y, map_y,
+                                                                                      M);
       mark_end();
       count_launch();
       cudaError_t e = cudaGetLastError();
@@ -860,10 +863,10 @@ int mixed_build_moments_rotated(const double* Lxo, const double* Lxv, const doub
     }
   }
   {
-    const long long tot = 2LL * N * N;
+    const long long tot = (long long)nm * N * N;
     const int g = (int)std::min<long long>((tot + 255) / 256, 152LL * 32);
-    mirror_tiles_kernel<<<g, 256, 0, s>>>(U_hole, N, 2);
-    mirror_tiles_kernel<<<g, 256, 0, s>>>(U_part, N, 2);
+    mirror_tiles_kernel<<<g, 256, 0, s>>>(U_hole, N, nm);
+    mirror_tiles_kernel<<<g, 256, 0, s>>>(U_part, N, nm);
     count_launch(2);
   }
   int herr = 0;
