@@ -46,61 +46,69 @@ def parse():
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--shift-mode", type=int, default=1, choices=[0, 1],
                     help="Fock-loop shift: 0 solve every cycle, 1 one Newton step per cycle")
+    ap.add_argument("--nmom", type=int, default=1, choices=[1, 3],
+                    help="conserved moments 0..nmom: 1 = AGF2(1,0), 3 = AGF2(2,0)")
     return ap.parse_args()
 
 
-def workload_desc(cfg):
+def workload_desc(cfg, nmom=1):
     from paper_2106_03508_gb300.synth import CONFIGS
     c = CONFIGS[cfg]
+    m = (nmom + 1) // 2
     return {"workload": f"{cfg}: synthetic closed-shell DF system nmo={c['nmo']} nocc={c['nocc']} "
-                        f"naux={c['naux']} seed={c['seed']}, steady-state AGF2(1,0) iterations",
-            "nmo": c["nmo"], "nocc": c["nocc"], "naux": c["naux"], "seed": c["seed"]}
+                        f"naux={c['naux']} seed={c['seed']}, steady-state AGF2({m},0) iterations",
+            "nmo": c["nmo"], "nocc": c["nocc"], "naux": c["naux"], "seed": c["seed"],
+            "nmom": nmom}
 
 
 # ---------------------------------------------------------------------------
 # CPU oracle sample (cpu_baseline and --impl reference)
 # ---------------------------------------------------------------------------
-def _oracle_setup(cfg):
+def _oracle_setup(cfg, nmom=1):
+    """Steady-state pole counts: nmo + (nmom+1) nmo poles, of which the nocc
+    occupied orbitals' poles and the (nmom+1)/2 nmo hole auxiliaries' poles
+    lie below mu."""
     from paper_2106_03508_gb300.synth import CONFIGS, make_config
     c = CONFIGS[cfg]
     s = make_config(cfg)
     N = s.nmo
-    return s, c["nocc"] + N, 3 * N - (c["nocc"] + N)
+    o_full = c["nocc"] + (nmom + 1) // 2 * N
+    return s, o_full, (nmom + 2) * N - o_full
 
 
-def oracle_time(cfg, k):
+def oracle_time(cfg, k, nmom=1):
     """Seconds per full iteration extrapolated from one timed FP64-oracle
     moment build (the O(N^5) step) on a steady-state-shaped pole set with k
-    occupied poles and all v' = 3N - (nocc + N) virtual poles; the rate is
-    scaled by the algorithmic flop ratio to o' = nocc + N.  Fock loop and
-    compression excluded (O(N^3); they would only lower the CPU rate)."""
+    occupied poles and all v' virtual poles; the rate is scaled by the
+    algorithmic flop ratio to the full o'.  Fock loop and compression
+    excluded (O(N^3); they would only lower the CPU rate)."""
     from oracle import agf2_oracle as O
     from paper_2106_03508_gb300.synth import random_poles
-    s, o_full, v_full = _oracle_setup(cfg)
+    s, o_full, v_full = _oracle_setup(cfg, nmom)
     e, C, mu = random_poles(s.nmo, k + v_full, k, 11)
     t0 = time.perf_counter()
-    O.build_moments(s.L, e, C, mu)
+    O.build_moments(s.L, e, C, mu, nmom)
     dt = time.perf_counter() - t0
-    rate = O.flops_moments(s.nmo, k, v_full, s.naux) / dt
-    return O.flops_moments(s.nmo, o_full, v_full, s.naux) / rate, dt
+    rate = O.flops_moments(s.nmo, k, v_full, s.naux, nmom) / dt
+    return O.flops_moments(s.nmo, o_full, v_full, s.naux, nmom) / rate, dt
 
 
-def oracle_calibrate(cfg, target_s):
+def oracle_calibrate(cfg, target_s, nmom=1):
     """Smallest sample size k (doubling) whose oracle build takes >= target_s / 2."""
-    s, o_full, v_full = _oracle_setup(cfg)
+    s, o_full, v_full = _oracle_setup(cfg, nmom)
     k = 1
     while True:
-        t_iter, dt = oracle_time(cfg, k)
+        t_iter, dt = oracle_time(cfg, k, nmom)
         if dt >= target_s / 2 or 2 * k > o_full:
             return k, t_iter, dt
         k *= 2
 
 
-def oracle_sample_desc(cfg, k, dt):
-    s, o_full, v_full = _oracle_setup(cfg)
-    return (f"FP64 oracle build_moments on nmo={s.nmo} naux={s.naux} with {k} occupied + "
-            f"{v_full} virtual poles ({dt:.1f} s), extrapolated by algorithmic flops to "
-            f"o'={o_full}, v'={v_full} (one steady-state iteration); moment build only")
+def oracle_sample_desc(cfg, k, dt, nmom=1):
+    s, o_full, v_full = _oracle_setup(cfg, nmom)
+    return (f"FP64 oracle build_moments (nmom={nmom}) on nmo={s.nmo} naux={s.naux} with {k} "
+            f"occupied + {v_full} virtual poles ({dt:.1f} s), extrapolated by algorithmic flops "
+            f"to o'={o_full}, v'={v_full} (one steady-state iteration); moment build only")
 
 
 def run_reference(args):
@@ -108,12 +116,12 @@ def run_reference(args):
     if rank != 0:
         return
     cores = os.cpu_count()
-    k, _, _ = oracle_calibrate(args.config, args.cpu_seconds / 4)
+    k, _, _ = oracle_calibrate(args.config, args.cpu_seconds / 4, args.nmom)
     for _ in range(args.warmup):
-        oracle_time(args.config, k)
+        oracle_time(args.config, k, args.nmom)
     times, dts = [], []
     for _ in range(args.steps):
-        t, dt = oracle_time(args.config, k)
+        t, dt = oracle_time(args.config, k, args.nmom)
         times.append(t)
         dts.append(dt)
     t = statistics.median(times)
@@ -122,9 +130,10 @@ def run_reference(args):
             "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup,
             "ms_per_step": t * 1e3, "higher_is_better": True, "scaling": "weak",
             "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-            "config": workload_desc(args.config),
+            "config": workload_desc(args.config, args.nmom),
             "cpu_baseline": {"value": val, "unit": UNIT, "cores": cores, "kind": "oracle",
-                             "sample": oracle_sample_desc(args.config, k, statistics.median(dts))},
+                             "sample": oracle_sample_desc(args.config, k, statistics.median(dts),
+                                                          args.nmom)},
             "e2e": {"value": val, "unit": UNIT, "h2d_bytes_per_step": 0,
                     "d2h_bytes_per_step": 0}}
     print(json.dumps(line), flush=True)
@@ -275,6 +284,7 @@ def run_ours(args):
 
     o = agf2.agf2_opts_default()
     o.precision = prec
+    o.nmom = args.nmom
     o.fock.shift_mode = args.shift_mode
     o.max_iter = max(1, args.warmup)
     o.resume = 0
@@ -311,8 +321,9 @@ def run_ours(args):
     # ---- end to end through the C ABI with host buffers ----
     e2e = None
     if not args.no_e2e:
-        e_out = torch.empty(3 * N, dtype=torch.float64).pin_memory()
-        e_dev = torch.empty(3 * N, dtype=torch.float64, device="cuda")
+        nq = (args.nmom + 2) * N  # poles of the state
+        e_out = torch.empty(nq, dtype=torch.float64).pin_memory()
+        e_dev = torch.empty(nq, dtype=torch.float64, device="cuda")
         L2 = torch.empty_like(L)
         hc2 = torch.empty_like(hc)
         eps2 = torch.empty_like(eps)
@@ -336,6 +347,7 @@ def run_ours(args):
     if args.fp64_steps > 0 and prec != agf2.AGF2_FP64:
         of = agf2.agf2_opts_default()
         of.precision = agf2.AGF2_FP64
+        of.nmom = args.nmom
         of.fock.shift_mode = args.shift_mode
         of.max_iter = 1
         of.resume = 1
@@ -374,7 +386,7 @@ def run_ours(args):
         "warmup": args.warmup, "ms_per_step": ms_per_step, "higher_is_better": True,
         "scaling": "weak", "vs_baseline": None,
         "dtype": "bf16x3" if prec == agf2.AGF2_BF16X3 else "f64", "data": "synthetic",
-        "config": {**workload_desc(args.config), "precision": args.precision,
+        "config": {**workload_desc(args.config, args.nmom), "precision": args.precision,
                    "fock_shift_mode": args.shift_mode,
                    "l2": "inputs larger than L2 (L = %.0f MB FP64)" % (L.numel() * 8 / 1e6),
                    "parallelism": "replicas" if world > 1 else "single"},
@@ -400,9 +412,10 @@ def run_ours(args):
         "last_energies": {k: results[-1][k] for k in ("E_tot", "ip", "ea", "mu")},
     }
     if rank == 0 and world == 1:
-        k, t_iter, dt = oracle_calibrate(args.config, args.cpu_seconds)
+        k, t_iter, dt = oracle_calibrate(args.config, args.cpu_seconds, args.nmom)
         line["cpu_baseline"] = {"value": 1.0 / t_iter, "unit": UNIT, "cores": os.cpu_count(),
-                                "kind": "oracle", "sample": oracle_sample_desc(args.config, k, dt)}
+                                "kind": "oracle",
+                                "sample": oracle_sample_desc(args.config, k, dt, args.nmom)}
     print(json.dumps(line), flush=True)
     h.close()
     if world > 1:

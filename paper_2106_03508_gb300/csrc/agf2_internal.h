@@ -31,8 +31,14 @@ struct DGemm {
   double alpha = 1.0, beta = 0.0;
   bool atomic = false;  // C += alpha A B with atomicAdd (beta ignored)
   int ksplit = 1;       // split K over this many CTAs (requires atomic)
+  bool upper = false;   // C is symmetric (M == N, one batch, sCn == 1): compute the
+                        // tiles on and above the diagonal, then mirror the rest
 };
 cudaError_t dgemm(const DGemm& g, cudaStream_t s);
+// Output tile edge dgemm uses for an M x N product (40 where it pads less than 64).
+int dgemm_tile(int M, int N);
+// K splits for an M x N product with a long K: about 1024 threads per SM.
+int dgemm_split(int M, int N, long long K, bool upper);
 
 // Moment epilogue of one block pair (I, J) of outer indices (FP64 path):
 // from X_IJ[p][(ii*nJ+jj)*n_in + c] = (p x_ii | y_jj c) and
@@ -75,6 +81,9 @@ cudaError_t coulomb_from_gamma(const double* L, const double* gamma, int naux, i
 // gamma_Q = 2 sum_{r,k} Cocc[r][k] Y[r][Q][k]
 cudaError_t gamma_from_y(const double* Y, const double* Cocc, int nmo, int naux, int k,
                          double* gamma, cudaStream_t s);
+// gamma_Q = sum_rs L[Q][r][s] D[r][s]
+cudaError_t gamma_from_density(const double* L, const double* D, int naux, int n,
+                               double* gamma, cudaStream_t s);
 // F = h + J - K/2  (elementwise)
 cudaError_t fock_combine(const double* h, const double* J, const double* K, long long n, double* F,
                          cudaStream_t s);

@@ -144,13 +144,6 @@ double seconds_since(std::chrono::steady_clock::time_point t0) {
   return std::chrono::duration<double>(std::chrono::steady_clock::now() - t0).count();
 }
 
-// K splits so that an M x N FP64 GEMM with a long K fills about two waves of CTAs.
-int split_for(int M, int N, long long K) {
-  const long long tiles = (long long)((M + 63) / 64) * ((N + 63) / 64);
-  const long long want = (2 * 152 + tiles - 1) / tiles;
-  return (int)std::max(1LL, std::min(want, K / 256));
-}
-
 // ---------------------------------------------------------------------------
 // Fock matrix, Eq. (fock_matrix), density fitted
 // ---------------------------------------------------------------------------
@@ -163,15 +156,7 @@ void fock_general(agf2_context* ctx, const double* h, const double* L, int naux,
   double* J = ws(ctx, "fock_J", nn);
   double* K = ws(ctx, "fock_K", nn);
   double* gam = ws(ctx, "fock_gamma", naux);
-  // gamma_Q = sum_rs L[Q][r][s] D[r][s]: one-row GEMM (M = 1) over t = (r,s)
-  {
-    DGemm g;
-    g.M = naux; g.N = 1; g.K = (int)nn;
-    g.A = L; g.sAm = nn; g.sAk = 1;
-    g.B = D; g.sBk = 1; g.sBn = 0;
-    g.C = gam; g.sCm = 1; g.sCn = 0;
-    CK(dgemm(g, s));
-  }
+  CK(gamma_from_density(L, D, naux, n, gam, s));
   CK(coulomb_from_gamma(L, gam, naux, n, J, s));
   // Z[p][Q][r] = sum_s L[Q][p][s] D[s][r]
   {
@@ -191,7 +176,8 @@ void fock_general(agf2_context* ctx, const double* h, const double* L, int naux,
     g.B = L; g.sBk = n; g.sBn = 1;
     g.C = K; g.sCm = n; g.sCn = 1;
     g.atomic = true;
-    g.ksplit = split_for(n, n, g.K);
+    g.upper = true;  // K is symmetric
+    g.ksplit = dgemm_split(n, n, g.K, true);
     CK(cudaMemsetAsync(K, 0, nn * sizeof(double), s));
     CK(dgemm(g, s));
   }
@@ -227,11 +213,23 @@ void fock_cocc(agf2_context* ctx, const double* h, const double* L, int naux, in
     g.C = K; g.sCm = n; g.sCn = 1;
     g.alpha = 2.0;
     g.atomic = true;
-    g.ksplit = split_for(n, n, g.K);
+    g.upper = true;
+    g.ksplit = dgemm_split(n, n, g.K, true);
     CK(cudaMemsetAsync(K, 0, nn * sizeof(double), s));
     CK(dgemm(g, s));
   }
   CK(fock_combine(h, J, K, nn, F, s));
+}
+
+// F[D] for D = 2 Cocc Cocc^T (Cocc [n][k], D given as well): through the
+// occupied couplings while k < n (about 3 n^2 k n_Q flops), else through D
+// (about 3 n^3 n_Q flops); both form only the symmetric half of K.
+void fock_density(agf2_context* ctx, const double* h, const double* L, int naux, int n,
+                  const double* D, const double* Cocc, int k, double* F) {
+  if (k < n)
+    fock_cocc(ctx, h, L, naux, n, Cocc, k, F);
+  else
+    fock_general(ctx, h, L, naux, n, D, F);
 }
 
 // ---------------------------------------------------------------------------
@@ -286,8 +284,8 @@ void sector_fp64(agf2_context* ctx, const Sector& S, int N, int naux, int nmom, 
         g.B = Y; g.sBk = 1; g.sBn = 2 * K1;
         g.C = U + (long long)n * N * N; g.sCm = N; g.sCn = 1;
         g.atomic = true;
-        const int tiles = ((N + 63) / 64) * ((N + 63) / 64);
-        g.ksplit = std::max(1, std::min<int>((int)(2 * K1 / 256), (2 * 152 + tiles - 1) / tiles));
+        g.upper = true;  // U^(n) = (Y w^n) Y^T is symmetric
+        g.ksplit = dgemm_split(N, N, 2 * K1, true);
         CK(dgemm(g, s));
       }
     }
@@ -814,7 +812,7 @@ FockOut fock_loop_impl(agf2_context* ctx, const double* h, const double* L, int 
       CK(dgemm(g, s));
     }
     auto tf0 = std::chrono::steady_clock::now();
-    fock_cocc(ctx, h, L, naux, nmo, Cocc, ab.k, Fout);
+    fock_density(ctx, h, L, naux, nmo, Dn, Cocc, ab.k, Fout);
     CK(max_abs_diff(Dn, D, nn, red + 512, red, s));
     const double dD = scalar(ctx, red + 512);
     if (tr)
@@ -856,7 +854,7 @@ FockOut fock_loop_impl(agf2_context* ctx, const double* h, const double* L, int 
       CK(axpby(Fin, Fout, o.damping, 1.0 - o.damping, nn, s));
     }
   }
-  fock_cocc(ctx, h, L, naux, nmo, ws(ctx, "fl_Cocc", 1), out.k, F);
+  fock_density(ctx, h, L, naux, nmo, D, ws(ctx, "fl_Cocc", 1), out.k, F);
   sync(ctx);
   return out;
 }

@@ -14,72 +14,87 @@ namespace agf2 {
 
 namespace {
 
-constexpr int BM = 64, BN = 64, BK = 16, NT = 256;
+constexpr int BK = 16;
 
-__global__ void __launch_bounds__(NT) dgemm_kernel(DGemm g) {
-  __shared__ double As[BK][BM];
-  __shared__ double Bs[BK][BN];
+// Register-tiled FP64 GEMM tile: TB x TB outputs per CTA, R x R per thread,
+// (TB/R)^2 threads.  TB = 64 (R = 4, 256 threads) for large operands, TB = 40
+// (R = 5, 64 threads) where it pads less (e.g. 200 = 5 x 40 orbitals).
+template <int TB, int R>
+__global__ void __launch_bounds__((TB / R) * (TB / R)) dgemm_kernel(DGemm g) {
+  constexpr int TT = TB / R;       // threads per tile edge
+  constexpr int NT = TT * TT;
+  __shared__ double As[BK][TB];
+  __shared__ double Bs[BK][TB];
   const int z = blockIdx.z;
   const int b1 = z / g.nb2, b2 = z - b1 * g.nb2;
   const double* __restrict__ A = g.A + b1 * g.sA1 + b2 * g.sA2;
   const double* __restrict__ B = g.B + b1 * g.sB1 + b2 * g.sB2;
   double* C = g.C + b1 * g.sC1 + b2 * g.sC2;
-  const int m0 = blockIdx.y * BM;
-  const int nblk = (g.N + BN - 1) / BN;
-  const int n0 = (blockIdx.x % nblk) * BN;
+  const int m0 = blockIdx.y * TB;
+  const int nblk = (g.N + TB - 1) / TB;
+  const int n0 = (blockIdx.x % nblk) * TB;
+  if (g.upper && m0 > n0) return;  // symmetric C: the lower tiles are mirrored afterwards
   const int ks = blockIdx.x / nblk;  // K split index
   const int kchunk = ((g.K + g.ksplit - 1) / g.ksplit + BK - 1) / BK * BK;
   const int kbeg = ks * kchunk, kend = min(g.K, kbeg + kchunk);
-  const int tid = threadIdx.x, tx = tid & 15, ty = tid >> 4;
+  const int tid = threadIdx.x, tx = tid % TT, ty = tid / TT;
   const bool a_kc = (g.sAk == 1);
   const bool b_nc = (g.sBn == 1);
-  double acc[4][4];
+  double acc[R][R];
 #pragma unroll
-  for (int i = 0; i < 4; ++i)
+  for (int i = 0; i < R; ++i)
 #pragma unroll
-    for (int j = 0; j < 4; ++j) acc[i][j] = 0.0;
+    for (int j = 0; j < R; ++j) acc[i][j] = 0.0;
 
   for (int k0 = kbeg; k0 < kend; k0 += BK) {
-#pragma unroll
-    for (int r = 0; r < 4; ++r) {
-      const int e = tid + r * NT;
+    for (int e = tid; e < BK * TB; e += NT) {
       int mm, kk;
-      if (a_kc) { mm = e / BK; kk = e % BK; } else { mm = e % BM; kk = e / BM; }
+      if (a_kc) { mm = e / BK; kk = e % BK; } else { mm = e % TB; kk = e / TB; }
       const int gm = m0 + mm, gk = k0 + kk;
       As[kk][mm] = (gm < g.M && gk < kend) ? A[gm * g.sAm + gk * g.sAk] : 0.0;
       int nn;
-      if (b_nc) { nn = e % BN; kk = e / BN; } else { nn = e / BK; kk = e % BK; }
+      if (b_nc) { nn = e % TB; kk = e / TB; } else { nn = e / BK; kk = e % BK; }
       const int gn = n0 + nn, gk2 = k0 + kk;
       Bs[kk][nn] = (gn < g.N && gk2 < kend) ? B[gk2 * g.sBk + gn * g.sBn] : 0.0;
     }
     __syncthreads();
 #pragma unroll
     for (int kk = 0; kk < BK; ++kk) {
-      double a[4], b[4];
+      double a[R], b[R];
 #pragma unroll
-      for (int i = 0; i < 4; ++i) a[i] = As[kk][ty + 16 * i];
+      for (int i = 0; i < R; ++i) a[i] = As[kk][ty + TT * i];
 #pragma unroll
-      for (int j = 0; j < 4; ++j) b[j] = Bs[kk][tx + 16 * j];
+      for (int j = 0; j < R; ++j) b[j] = Bs[kk][tx + TT * j];
 #pragma unroll
-      for (int i = 0; i < 4; ++i)
+      for (int i = 0; i < R; ++i)
 #pragma unroll
-        for (int j = 0; j < 4; ++j) acc[i][j] = fma(a[i], b[j], acc[i][j]);
+        for (int j = 0; j < R; ++j) acc[i][j] = fma(a[i], b[j], acc[i][j]);
     }
     __syncthreads();
   }
 #pragma unroll
-  for (int i = 0; i < 4; ++i) {
-    const int gm = m0 + ty + 16 * i;
+  for (int i = 0; i < R; ++i) {
+    const int gm = m0 + ty + TT * i;
     if (gm >= g.M) continue;
 #pragma unroll
-    for (int j = 0; j < 4; ++j) {
-      const int gn = n0 + tx + 16 * j;
+    for (int j = 0; j < R; ++j) {
+      const int gn = n0 + tx + TT * j;
       if (gn >= g.N) continue;
       double* c = C + gm * g.sCm + gn * g.sCn;
       const double v = g.alpha * acc[i][j];
       if (g.atomic) atomicAdd(c, v);
       else *c = (g.beta == 0.0) ? v : fma(g.beta, *c, v);
     }
+  }
+}
+
+// C[p][q] <- C[q][p] for the lower tiles (p / tb > q / tb) an upper-tile GEMM skipped.
+__global__ void mirror_lower_tiles_kernel(double* C, int n, long long ld, int tb) {
+  const long long total = (long long)n * n;
+  for (long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x; t < total;
+       t += (long long)gridDim.x * blockDim.x) {
+    const int p = (int)(t / n), q = (int)(t % n);
+    if (p / tb > q / tb) C[p * ld + q] = C[q * ld + p];
   }
 }
 
@@ -225,6 +240,18 @@ __device__ inline double block_sum(double s) {
     for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
   }
   return s;
+}
+
+// gamma_Q = sum_rs L[Q][r][s] D[r][s]: one block per Q (a pass over L at HBM rate)
+__global__ void __launch_bounds__(RED_THREADS) gamma_density_kernel(const double* __restrict__ L,
+                                                                     const double* __restrict__ D,
+                                                                     long long nn,
+                                                                     double* __restrict__ gam) {
+  const double* LQ = L + (long long)blockIdx.x * nn;
+  double s = 0.0;
+  for (long long t = threadIdx.x; t < nn; t += blockDim.x) s = fma(LQ[t], D[t], s);
+  s = block_sum(s);
+  if (threadIdx.x == 0) gam[blockIdx.x] = s;
 }
 
 __device__ inline double block_max(double s) {
@@ -394,7 +421,9 @@ cudaError_t dgemm(const DGemm& g, cudaStream_t s) {
   if (g.M <= 0 || g.N <= 0 || g.nb1 <= 0 || g.nb2 <= 0) return cudaSuccess;
   const long long nz = (long long)g.nb1 * g.nb2;
   if (g.ksplit > 1 && !g.atomic) return cudaErrorInvalidValue;
-  dim3 grid(((g.N + BN - 1) / BN) * std::max(1, g.ksplit), (g.M + BM - 1) / BM, 1);
+  if (g.upper && (g.M != g.N || nz != 1 || g.sCn != 1)) return cudaErrorInvalidValue;
+  const int tb = dgemm_tile(g.M, g.N);
+  dim3 grid(((g.N + tb - 1) / tb) * std::max(1, g.ksplit), (g.M + tb - 1) / tb, 1);
   // gridDim.z is limited to 65535: split large batches over several launches,
   // each covering whole b1 rows.
   const long long lim = (65535LL / g.nb2) * g.nb2;
@@ -408,11 +437,32 @@ cudaError_t dgemm(const DGemm& g, cudaStream_t s) {
     h.C += b1_0 * g.sC1;
     h.nb1 = (int)(chunk / g.nb2);
     grid.z = (unsigned)chunk;
-    dgemm_kernel<<<grid, NT, 0, s>>>(h);
+    if (tb == 40)
+      dgemm_kernel<40, 5><<<grid, 64, 0, s>>>(h);
+    else
+      dgemm_kernel<64, 4><<<grid, 256, 0, s>>>(h);
     count_launch();
     z0 += chunk;
   }
+  if (g.upper) {
+    mirror_lower_tiles_kernel<<<grid_for((long long)g.M * g.M), 256, 0, s>>>(g.C, g.M, g.sCm, tb);
+    count_launch();
+  }
   return cudaGetLastError();
+}
+
+int dgemm_tile(int M, int N) {
+  auto padded = [&](long long t) { return ((M + t - 1) / t * t) * ((N + t - 1) / t * t); };
+  return padded(40) < padded(64) ? 40 : 64;
+}
+
+int dgemm_split(int M, int N, long long K, bool upper) {
+  const int tb = dgemm_tile(M, N);
+  const long long threads = tb == 40 ? 64 : 256;
+  const long long tm = (M + tb - 1) / tb, tn = (N + tb - 1) / tb;
+  const long long tiles = upper ? tm * (tm + 1) / 2 : tm * tn;
+  const long long want = (152LL * 1024 / threads + tiles - 1) / tiles;
+  return (int)std::max(1LL, std::min(want, K / 256));
 }
 
 cudaError_t sd_epilogue_fp64(const double* XIJ, const double* XJI, int nmo, int nI, int nJ,
@@ -498,6 +548,13 @@ cudaError_t upper_from_lower_t(const double* Lc, int n, double* dst, long long l
 
 cudaError_t physical_block(const double* V, int ld, int nmo, int ncol, double* out, cudaStream_t s) {
   physical_block_kernel<<<grid_for((long long)nmo * ncol), 256, 0, s>>>(V, ld, nmo, ncol, out);
+  count_launch();
+  return cudaGetLastError();
+}
+
+cudaError_t gamma_from_density(const double* L, const double* D, int naux, int n,
+                               double* gamma, cudaStream_t s) {
+  gamma_density_kernel<<<naux, RED_THREADS, 0, s>>>(L, D, (long long)n * n, gamma);
   count_launch();
   return cudaGetLastError();
 }
