@@ -119,6 +119,23 @@ int agf2_compress(agf2_handle h, const double* U, int nmo, double* E_aux, double
 int agf2_compress_moments(agf2_handle h, const double* U, int nmo, int nmom, double* E_aux,
                           double* v_aux);
 
+/*
+ * Eigenpairs of a real symmetric matrix, for the extended Hamiltonian
+ * [[F, v], [v^T, diag(E)]] of Eqs. (dyson_eq_eig) / (post_compression_h)
+ * whose eigenvalues are the Green's-function poles and whose eigenvectors'
+ * physical rows are the pole couplings.  This is the eigensolver the Fock
+ * loop uses: Householder tridiagonalisation in one cooperative kernel,
+ * divide and conquer with Gu-Eisenstat eigenvectors, back-transformation of
+ * the first nphys rows only.
+ *   A [n][n]        in   symmetric (row- or column-major alike), unchanged
+ *   w [n]           out  eigenvalues, ascending
+ *   V [n][n]        out  column-major: eigenvector x in V[x n .. x n + n),
+ *                        of which only the first nphys entries are written
+ * Returns AGF2_ERR_INVALID_ARG unless 1 <= nphys <= n <= 8000, and
+ * AGF2_ERR_TIMEOUT if the tridiagonalisation's grid barrier gave up.
+ */
+int agf2_eigh_physical(agf2_handle h, const double* A, int n, int nphys, double* w, double* V);
+
 typedef struct {
     double tol_D;      /* convergence: max |D_new - D| (default 1e-10)        */
     int    max_cycle;  /* Fock cycles (default 100)                           */

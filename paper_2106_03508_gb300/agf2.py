@@ -32,7 +32,7 @@ EXPORTED = [
     "agf2_fock_opts_default", "agf2_fock_loop", "agf2_opts_default", "agf2_run",
     "agf2_get_state", "agf2_set_profiling", "agf2_kernel_stats", "agf2_launch_count",
     "agf2_build_moments_noalloc", "agf2_run_batched", "agf2_spectral_function",
-    "agf2_compress_moments",
+    "agf2_compress_moments", "agf2_eigh_physical",
 ]
 
 
@@ -85,6 +85,7 @@ def _load():
         "agf2_build_moments": (I, [P, P, I, I, P, P, I, D, I, I, P, P]),
         "agf2_compress": (I, [P, P, I, P, P]),
         "agf2_compress_moments": (I, [P, P, I, I, P, P]),
+        "agf2_eigh_physical": (I, [P, P, I, I, P, P]),
         "agf2_fock_opts_default": (V, [ct.POINTER(agf2_fock_opts)]),
         "agf2_fock_loop": (I, [P, P, P, I, I, I, P, P, I, P, P, P, P,
                                ct.POINTER(agf2_fock_opts), ct.POINTER(agf2_fock_info)]),
@@ -159,6 +160,10 @@ def agf2_compress(h, U, nmo, E_aux, v_aux, allow=()):
 
 def agf2_compress_moments(h, U, nmo, nmom, E_aux, v_aux, allow=()):
     return _check(h, _lib.agf2_compress_moments(h, U, nmo, nmom, E_aux, v_aux), allow)
+
+
+def agf2_eigh_physical(h, A, n, nphys, w, V):
+    return _check(h, _lib.agf2_eigh_physical(h, A, n, nphys, w, V))
 
 
 def agf2_fock_opts_default() -> agf2_fock_opts:

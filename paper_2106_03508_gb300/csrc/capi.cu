@@ -46,6 +46,7 @@ struct agf2_context {
   int iter = 0;
   KernelStats stats;
   void* mixed_ws = nullptr;
+  void* eig_ws = nullptr;
 };
 
 namespace {
@@ -564,9 +565,12 @@ struct Eig {
 Eig diag_extended(agf2_context* ctx, const double* F, const double* E, const double* v, double delta,
                   int nmo, int nse) {
   const int n = nmo + nse;
-  Eig r{ws(ctx, "ext_H", (size_t)n * n), ws(ctx, "ext_w", n), n};
-  CK(build_extended_h(F, E, v, delta, nmo, nse, r.V, ctx->stream));
-  syevd(ctx, r.V, n, r.w);
+  double* H = ws(ctx, "ext_H", (size_t)n * n);
+  Eig r{ws(ctx, "ext_V", (size_t)n * n), ws(ctx, "ext_w", n), n};
+  CK(build_extended_h(F, E, v, delta, nmo, nse, H, ctx->stream));
+  if (!ctx->eig_ws) ctx->eig_ws = eig_workspace_create();
+  const int rc = eigh_phys(ctx->eig_ws, H, n, nmo, r.w, r.V, ctx->stream, ctx->err);
+  if (rc != AGF2_OK) throw Fail{rc};
   return r;
 }
 
@@ -774,7 +778,7 @@ FockOut fock_loop_impl(agf2_context* ctx, const double* h, const double* L, int 
       sh = solve_shift(ctx, Fin, E, v, nmo, nse, nelec, o.shift_tol);
       CK(add_scalar(E, sh.delta, nse, s));
       // the shift solve's last decomposition is the one at the chosen delta
-      eg = sh.last_is_best ? Eig{ws(ctx, "ext_H", (size_t)n * n), ws(ctx, "ext_w", n), n}
+      eg = sh.last_is_best ? Eig{ws(ctx, "ext_V", (size_t)n * n), ws(ctx, "ext_w", n), n}
                            : diag_extended(ctx, Fin, E, v, 0.0, nmo, nse);
     }
     const double t_shift = seconds_since(tc0);
@@ -935,6 +939,7 @@ int agf2_destroy(agf2_handle h) {
   for (auto& kv : h->bufs)
     if (kv.second.p) cudaFree(kv.second.p);
   mixed_workspace_destroy(h->mixed_ws);
+  eig_workspace_destroy(h->eig_ws);
   if (h->dev_info) cudaFree(h->dev_info);
   if (h->blas) cublasDestroy(h->blas);
   if (h->solver) cusolverDnDestroy(h->solver);
@@ -1031,6 +1036,18 @@ int agf2_compress_moments(agf2_handle h, const double* U, int nmo, int nmom, dou
     check_dev_ptr(ctx, E_aux, "E_aux");
     check_dev_ptr(ctx, v_aux, "v_aux");
     compress_lanczos_impl(ctx, U, nmo, nmom, E_aux, v_aux, (long long)(nmom + 1) / 2 * nmo);
+  });
+}
+
+int agf2_eigh_physical(agf2_handle h, const double* A, int n, int nphys, double* w, double* V) {
+  return guarded(h, [&](agf2_context* ctx) {
+    if (n < 1 || nphys < 1 || nphys > n) fail(ctx, AGF2_ERR_INVALID_ARG, "need 1 <= nphys <= n");
+    check_dev_ptr(ctx, A, "A");
+    check_dev_ptr(ctx, w, "w");
+    check_dev_ptr(ctx, V, "V");
+    if (!ctx->eig_ws) ctx->eig_ws = eig_workspace_create();
+    const int rc = eigh_phys(ctx->eig_ws, A, n, nphys, w, V, ctx->stream, ctx->err);
+    if (rc != AGF2_OK) throw Fail{rc};
   });
 }
 
