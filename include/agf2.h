@@ -273,14 +273,21 @@ int agf2_spectral_function(agf2_handle h, const double* e, const double* C, int 
                            double* A_orb);
 
 /*
- * Opt-in timing of the split-precision tensor-core kernels: with enable = 1
- * every launch of the pair GEMM (kind 0: GEMM 1 of the moment build with its
- * S/D and energy-weight epilogue) and of the moment GEMM (kind 1: GEMM 2 into
- * U) is bracketed by CUDA events on the handle's stream; agf2_kernel_stats
- * returns, since the last agf2_set_profiling call, the number of launches,
- * their summed duration (ms) and their algorithmic flop count (the ordered
- * pole pairs' share of N o' v' (o'+v') [2 n_Q + 2 (nmom+1) N]).  Timing
- * adds event records and is off by default.
+ * Opt-in timing with CUDA events on the handle's stream.  With enable = 1,
+ * agf2_kernel_stats returns, since the last agf2_set_profiling call, the
+ * number of timed regions of a kind, their summed duration (ms) and their
+ * algorithmic flop count:
+ *   kind 0: pair GEMM launches of the split-precision moment build (GEMM 1
+ *           with its S/D and energy-weight epilogue; the ordered pole pairs'
+ *           share of N o' v' (o'+v') 2 n_Q),
+ *   kind 1: moment GEMM launches (GEMM 2 into U; 2 (nmom+1) N^2 per
+ *           ordered pair and inner pole),
+ *   kind 2: the FP64 GEMMs of each DF Fock build, Eq. (fock_matrix)
+ *           (2 n^2 m n_Q for L C or L D, m = k or n, plus n (n+1) m n_Q for
+ *           the symmetric half of K),
+ *   kind 3: each extended-Hamiltonian eigendecomposition of the Fock loop
+ *           (4/3 n^3 + 4 nmo n^2).
+ * Timing adds event records and is off by default.
  */
 int agf2_set_profiling(agf2_handle h, int enable);
 int agf2_kernel_stats(agf2_handle h, int kind, long long* launches, double* ms, double* flops);

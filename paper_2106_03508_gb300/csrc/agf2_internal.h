@@ -12,10 +12,13 @@ void count_launch(long long n = 1);
 // Per-kernel-kind timing of the split-precision kernels (opt-in): CUDA events
 // bracket every launch; durations are summed when the stream is synchronised.
 struct KernelStats {
+  static constexpr int kKinds = 4;
   bool enabled = false;
-  long long launches[2] = {0, 0};   // 0: pair GEMM (GEMM 1 + epilogue), 1: moment GEMM
-  double ms[2] = {0.0, 0.0};
-  double flops[2] = {0.0, 0.0};     // algorithmic flops of those launches
+  // 0: pair GEMM (GEMM 1 + epilogue), 1: moment GEMM, 2: FP64 Fock-build
+  // GEMMs (per Fock build), 3: extended-Hamiltonian eigensolver (per call)
+  long long launches[kKinds] = {0, 0, 0, 0};
+  double ms[kKinds] = {0.0, 0.0, 0.0, 0.0};
+  double flops[kKinds] = {0.0, 0.0, 0.0, 0.0};  // algorithmic flops of those launches
 };
 
 // Generic strided, two-level-batched FP64 GEMM:

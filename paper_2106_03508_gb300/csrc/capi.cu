@@ -45,6 +45,8 @@ struct agf2_context {
   bool have_uprev = false;
   int iter = 0;
   KernelStats stats;
+  struct Pending { cudaEvent_t a, b; int kind; double flops; };
+  std::vector<Pending> pending;  // timed regions not yet read back
   void* mixed_ws = nullptr;
   void* eig_ws = nullptr;
 };
@@ -108,7 +110,44 @@ T* ws(agf2_context* ctx, const char* name, size_t count) {
   return static_cast<T*>(b.p);
 }
 
-void sync(agf2_context* ctx) { CK(cudaStreamSynchronize(ctx->stream)); }
+// Timed regions of kinds 2 and 3 (see KernelStats): events on the handle's
+// stream, read back at the next synchronisation.
+struct TimedRegion {
+  agf2_context* ctx;
+  cudaEvent_t a = nullptr, b = nullptr;
+  int kind;
+  double flops;
+  TimedRegion(agf2_context* c, int k, double f) : ctx(c), kind(k), flops(f) {
+    if (!ctx->stats.enabled) return;
+    cudaEventCreate(&a);
+    cudaEventCreate(&b);
+    cudaEventRecord(a, ctx->stream);
+  }
+  ~TimedRegion() {
+    if (!a) return;
+    cudaEventRecord(b, ctx->stream);
+    ctx->pending.push_back({a, b, kind, flops});
+  }
+};
+
+void flush_stats(agf2_context* ctx) {
+  for (auto& p : ctx->pending) {
+    float ms = 0.f;
+    if (cudaEventElapsedTime(&ms, p.a, p.b) == cudaSuccess) {
+      ctx->stats.launches[p.kind] += 1;
+      ctx->stats.ms[p.kind] += ms;
+      ctx->stats.flops[p.kind] += p.flops;
+    }
+    cudaEventDestroy(p.a);
+    cudaEventDestroy(p.b);
+  }
+  ctx->pending.clear();
+}
+
+void sync(agf2_context* ctx) {
+  CK(cudaStreamSynchronize(ctx->stream));
+  if (!ctx->pending.empty()) flush_stats(ctx);
+}
 
 template <class T>
 std::vector<T> to_host(agf2_context* ctx, const T* d, size_t n) {
@@ -159,6 +198,8 @@ void fock_general(agf2_context* ctx, const double* h, const double* L, int naux,
   double* gam = ws(ctx, "fock_gamma", naux);
   CK(gamma_from_density(L, D, naux, n, gam, s));
   CK(coulomb_from_gamma(L, gam, naux, n, J, s));
+  // algorithmic flops: Z = L D (2 n^3 n_Q) and the symmetric half of K (n^2 (n+1) n_Q)
+  TimedRegion tr(ctx, 2, (2.0 * n + (n + 1.0)) * (double)n * n * naux);
   // Z[p][Q][r] = sum_s L[Q][p][s] D[s][r]
   {
     DGemm g;
@@ -195,6 +236,8 @@ void fock_cocc(agf2_context* ctx, const double* h, const double* L, int naux, in
   double* J = ws(ctx, "fock_J", nn);
   double* K = ws(ctx, "fock_K", nn);
   double* gam = ws(ctx, "fock_gamma", naux);
+  // algorithmic flops: Y = L Cocc (2 n^2 k n_Q) and the symmetric half of K (n (n+1) k n_Q)
+  TimedRegion tr(ctx, 2, (2.0 * n + (n + 1.0)) * (double)n * k * naux);
   {
     DGemm g;  // Y[p][Q][c] = sum_r L[Q][p][r] Cocc[r][c]
     g.M = n; g.N = k; g.K = n;
@@ -569,8 +612,13 @@ Eig diag_extended(agf2_context* ctx, const double* F, const double* E, const dou
   Eig r{ws(ctx, "ext_V", (size_t)n * n), ws(ctx, "ext_w", n), n};
   CK(build_extended_h(F, E, v, delta, nmo, nse, H, ctx->stream));
   if (!ctx->eig_ws) ctx->eig_ws = eig_workspace_create();
-  const int rc = eigh_phys(ctx->eig_ws, H, n, nmo, r.w, r.V, ctx->stream, ctx->err);
-  if (rc != AGF2_OK) throw Fail{rc};
+  {
+    // algorithmic flops: tridiagonalisation 4/3 n^3, physical rows 2 nmo n^2
+    // and their product with the tridiagonal eigenvectors 2 nmo n^2
+    TimedRegion tr(ctx, 3, (4.0 / 3.0) * n * (double)n * n + 4.0 * nmo * (double)n * n);
+    const int rc = eigh_phys(ctx->eig_ws, H, n, nmo, r.w, r.V, ctx->stream, ctx->err);
+    if (rc != AGF2_OK) throw Fail{rc};
+  }
   return r;
 }
 
@@ -940,6 +988,10 @@ int agf2_destroy(agf2_handle h) {
     if (kv.second.p) cudaFree(kv.second.p);
   mixed_workspace_destroy(h->mixed_ws);
   eig_workspace_destroy(h->eig_ws);
+  for (auto& p : h->pending) {
+    cudaEventDestroy(p.a);
+    cudaEventDestroy(p.b);
+  }
   if (h->dev_info) cudaFree(h->dev_info);
   if (h->blas) cublasDestroy(h->blas);
   if (h->solver) cusolverDnDestroy(h->solver);
@@ -1240,6 +1292,7 @@ int agf2_spectral_function(agf2_handle h, const double* e, const double* C, int 
 
 int agf2_set_profiling(agf2_handle h, int enable) {
   return guarded(h, [&](agf2_context* ctx) {
+    sync(ctx);
     ctx->stats = KernelStats();
     ctx->stats.enabled = enable != 0;
   });
@@ -1247,7 +1300,7 @@ int agf2_set_profiling(agf2_handle h, int enable) {
 
 int agf2_kernel_stats(agf2_handle h, int kind, long long* launches, double* ms, double* flops) {
   return guarded(h, [&](agf2_context* ctx) {
-    if (kind < 0 || kind > 1) fail(ctx, AGF2_ERR_INVALID_ARG, "kind must be 0 or 1");
+    if (kind < 0 || kind >= KernelStats::kKinds) fail(ctx, AGF2_ERR_INVALID_ARG, "kind must be 0..3");
     if (launches) *launches = ctx->stats.launches[kind];
     if (ms) *ms = ctx->stats.ms[kind];
     if (flops) *flops = ctx->stats.flops[kind];
