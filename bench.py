@@ -29,6 +29,11 @@ sys.path.insert(0, str(ROOT))
 
 METRIC = "AGF2 iterations/sec and moment-build TFLOP/s, mixed vs FP64 at ≤1e-5 Ha IP err"
 FP64_NOMINAL_TFLOPS = 1.25  # GB300 FP64 (and FP64 tensor) nominal rate
+# DRAM bytes (read + write) per timed region of a kernel kind, from one ncu
+# --set full capture of the unchanged kernels at that workload's shapes
+# (profiles/dgemm_fock_build_c2.md: the two GEMMs of one c2 Fock build through
+# the density, the path the steady-state c2 iteration takes)
+NCU_TRAFFIC = {("c2", 2): 0.256458e9 + 0.218084e9 + 1.036790e9 + 0.004292e9}
 UNIT = "iterations/s"
 
 
@@ -415,7 +420,7 @@ def run_ours(args):
                                    for k in ("t_moments", "t_compress", "t_fock", "t_energy")},
         "moment_build": {"tflops_algorithmic": mom_fl / mom_t / 1e12, "flops_per_iter": mom_fl,
                          "seconds": mom_t},
-        "roofline": {**roof(dominant), "traffic": None,
+        "roofline": {**roof(dominant), "traffic": NCU_TRAFFIC.get((args.config, dominant)),
                      "note": "dominant kernel of the step by device time; achieved = algorithmic "
                              "flops / CUDA-event time (the split-BF16 kernels issue 6 limb "
                              "products per algorithmic product)"},
