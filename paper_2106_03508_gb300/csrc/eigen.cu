@@ -728,6 +728,106 @@ __global__ void phys_rows_kernel(const double* __restrict__ Vr, const double* __
     for (int k = lane; k < n; k += 32) X[(long long)p * n + k] = x[k];
 }
 
+constexpr int WY = 8;  // reflectors per compact-WY block of the back-transformation
+
+// T factors of the compact WY form, one CTA per block of WY reflectors
+// j0 = c WY .. j0 + WY - 1 (missing ones count as tau = 0):
+// H_{j0} H_{j0+1} ... = I - V T V^T with T upper triangular,
+//   T[i][i] = tau_i,  T[0:i, i] = -tau_i T[0:i, 0:i] (V[:, 0:i]^T v_i).
+__global__ void wy_t_kernel(const double* __restrict__ Vr, const double* __restrict__ tau, int n,
+                            double* __restrict__ Tout) {
+  __shared__ double Gm[WY][WY];
+  const int c = blockIdx.x, j0 = c * WY, nref = n - 2;
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31, nw = blockDim.x >> 5;
+  for (int q = warp; q < WY * WY; q += nw) {
+    const int l = q / WY, i = q % WY;
+    if (l >= i) continue;  // warp-uniform
+    double g = 0.0;
+    if (j0 + i < nref) {
+      const double* vl = Vr + (long long)(j0 + l) * n;
+      const double* vi = Vr + (long long)(j0 + i) * n;
+      for (int k = j0 + i + 1 + lane; k < n; k += 32) g = fma(vl[k], vi[k], g);
+    }
+    g = warp_sum(g);
+    if (lane == 0) Gm[l][i] = g;
+  }
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    double T[WY][WY];
+    for (int r = 0; r < WY; ++r)
+      for (int i = 0; i < WY; ++i) T[r][i] = 0.0;
+    for (int i = 0; i < WY; ++i) {
+      const double ti = (j0 + i < nref) ? tau[j0 + i] : 0.0;
+      double w[WY];
+      for (int l = 0; l < i; ++l) w[l] = -ti * Gm[l][i];
+      for (int r = 0; r < i; ++r) {
+        double acc = 0.0;
+        for (int l = r; l < i; ++l) acc = fma(T[r][l], w[l], acc);
+        T[r][i] = acc;
+      }
+      T[i][i] = ti;
+    }
+    for (int r = 0; r < WY; ++r)
+      for (int i = 0; i < WY; ++i) Tout[(long long)c * WY * WY + r * WY + i] = T[r][i];
+  }
+}
+
+// Physical rows of Q block by block: x <- x (I - V T V^T) = x - ((x V) T) V^T,
+// one warp per row (the CTA's rows and the block's reflectors and T in
+// shared memory); the WY dot products and updates run side by side, so a
+// row waits on one reduction per block instead of one per reflector.
+__global__ void phys_rows_wy_kernel(const double* __restrict__ Vr, const double* __restrict__ Tall,
+                                    int n, int nphys, int wpb, double* __restrict__ X) {
+  extern __shared__ double xs[];
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int p = warp < wpb ? blockIdx.x * wpb + warp : nphys;  // other warps only stage
+  double* vsm = xs + (long long)wpb * n;   // [WY][n]
+  double* Tsm = vsm + (long long)WY * n;   // [WY][WY]
+  double* x = xs + (long long)min(warp, wpb - 1) * n;
+  if (warp < wpb)
+    for (int k = lane; k < n; k += 32) x[k] = (k == p) ? 1.0 : 0.0;
+  const int nref = n - 2, nblk = (nref + WY - 1) / WY;
+  for (int c = 0; c < nblk; ++c) {
+    const int j0 = c * WY;
+    __syncthreads();
+    for (long long e = threadIdx.x; e < (long long)WY * n; e += blockDim.x) {
+      const int i = (int)(e / n), k = (int)(e % n), j = j0 + i;
+      vsm[e] = (j < nref && k > j) ? Vr[(long long)j * n + k] : 0.0;
+    }
+    for (int e = threadIdx.x; e < WY * WY; e += blockDim.x) Tsm[e] = Tall[(long long)c * WY * WY + e];
+    __syncthreads();
+    if (p < nphys) {
+      double y[WY];
+#pragma unroll
+      for (int i = 0; i < WY; ++i) y[i] = 0.0;
+      for (int k = j0 + 1 + lane; k < n; k += 32) {
+        const double xk = x[k];
+#pragma unroll
+        for (int i = 0; i < WY; ++i) y[i] = fma(xk, vsm[i * n + k], y[i]);
+      }
+#pragma unroll
+      for (int i = 0; i < WY; ++i) y[i] = warp_sum(y[i]);
+      double z[WY];
+#pragma unroll
+      for (int i = 0; i < WY; ++i) {
+        double acc = 0.0;
+#pragma unroll
+        for (int l = 0; l <= i; ++l) acc = fma(y[l], Tsm[l * WY + i], acc);
+        z[i] = acc;
+      }
+      for (int k = j0 + 1 + lane; k < n; k += 32) {
+        double a = x[k];
+#pragma unroll
+        for (int i = 0; i < WY; ++i) a = fma(-z[i], vsm[i * n + k], a);
+        x[k] = a;
+      }
+      __syncwarp();
+    }
+  }
+  if (p < nphys)
+    for (int k = lane; k < n; k += 32) X[(long long)p * n + k] = x[k];
+}
+
 struct Buf {
   void* p = nullptr;
   size_t bytes = 0;
@@ -765,7 +865,7 @@ struct EigWs {
   std::vector<Level> levels;
   Buf plan_mem;
   int* split = nullptr;  // device [n] split flags, inside plan_mem
-  Buf A, d, e, tau, Vr, P, part, nxt, bar, err, w, Qa, Qb, M, X;
+  Buf A, d, e, tau, Vr, P, part, nxt, bar, err, w, Qa, Qb, M, X, Twy;
   Buf f_dsrt, f_zsrt, f_dk, f_zk, f_rc, f_rs, f_tv, f_zh, f_inv, f_mtmp, f_rho, f_sgn;
   Buf i_perm, i_kept, i_dpos, i_ra, i_rb, i_org, i_rank, i_k, i_rot;
 };
@@ -844,7 +944,7 @@ void* eig_workspace_create() { return new EigWs(); }
 void eig_workspace_destroy(void* p) {
   if (!p) return;
   EigWs* W = static_cast<EigWs*>(p);
-  for (Buf* b : {&W->plan_mem, &W->A, &W->d, &W->e, &W->tau, &W->Vr, &W->P, &W->part, &W->nxt,
+  for (Buf* b : {&W->plan_mem, &W->Twy, &W->A, &W->d, &W->e, &W->tau, &W->Vr, &W->P, &W->part, &W->nxt,
                  &W->bar, &W->err, &W->w, &W->Qa, &W->Qb, &W->M, &W->X, &W->f_dsrt, &W->f_zsrt,
                  &W->f_dk, &W->f_zk, &W->f_rc, &W->f_rs, &W->f_tv, &W->f_zh, &W->f_inv,
                  &W->f_mtmp, &W->f_rho, &W->f_sgn, &W->i_perm, &W->i_kept, &W->i_dpos, &W->i_ra,
@@ -984,19 +1084,38 @@ int eigh_phys(void* workspace, const double* Ain, int n, int nphys, double* w_ou
   if (!ck("divide and conquer")) return AGF2_ERR_CUDA;
   // 3. physical rows of Q, then V_phys = X Z (column-major output, ld n)
   {
-    // rows per CTA: few, so that the rows' FP64 work spreads over the SMs;
-    // reflectors staged per chunk: as many (up to 8) as fit beside the rows
+    // rows per CTA: few, so that the rows' FP64 work spreads over the SMs
     const long long per = (long long)n * sizeof(double);
     const int wpb = std::max(1, std::min(4, (nphys + 2 * nsm - 1) / (2 * nsm)));
-    const int ch = (int)std::max(1LL, std::min(8LL, ((long long)smem_max - 1024) / per - wpb));
-    const size_t psm = (size_t)(wpb + ch) * per;
-    if (psm > 48 * 1024 &&
-        cudaFuncSetAttribute(phys_rows_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                             (int)psm) != cudaSuccess) {
-      err = "eigh_phys: shared memory attribute (back-transformation)";
-      return AGF2_ERR_CUDA;
+    const size_t wsm = (size_t)(wpb + WY) * per + WY * WY * sizeof(double);
+    if (wsm + 1024 <= (size_t)smem_max) {
+      // compact-WY blocks of 8 reflectors
+      const int nblk = (n - 2 + WY - 1) / WY;
+      double* Tw = grow<double>(W.Twy, (size_t)std::max(1, nblk) * WY * WY, err);
+      if (!Tw) return AGF2_ERR_OOM;
+      if (nblk > 0) {
+        wy_t_kernel<<<nblk, 256, 0, s>>>(Vr, tau, n, Tw);
+        count_launch();
+      }
+      if (wsm > 48 * 1024 &&
+          cudaFuncSetAttribute(phys_rows_wy_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                               (int)wsm) != cudaSuccess) {
+        err = "eigh_phys: shared memory attribute (back-transformation)";
+        return AGF2_ERR_CUDA;
+      }
+      phys_rows_wy_kernel<<<(nphys + wpb - 1) / wpb, 256, wsm, s>>>(Vr, Tw, n, nphys, wpb, X);
+    } else {
+      // one reflector at a time, staged `ch` per barrier (large n)
+      const int ch = (int)std::max(1LL, std::min(8LL, ((long long)smem_max - 1024) / per - wpb));
+      const size_t psm = (size_t)(wpb + ch) * per;
+      if (psm > 48 * 1024 &&
+          cudaFuncSetAttribute(phys_rows_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                               (int)psm) != cudaSuccess) {
+        err = "eigh_phys: shared memory attribute (back-transformation)";
+        return AGF2_ERR_CUDA;
+      }
+      phys_rows_kernel<<<(nphys + wpb - 1) / wpb, 256, psm, s>>>(Vr, tau, n, nphys, ch, wpb, X);
     }
-    phys_rows_kernel<<<(nphys + wpb - 1) / wpb, 256, psm, s>>>(Vr, tau, n, nphys, ch, wpb, X);
     count_launch();
     DGemm g;
     g.M = nphys; g.N = n; g.K = n;
