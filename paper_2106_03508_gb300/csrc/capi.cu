@@ -1,10 +1,11 @@
 // C ABI of the AGF2 library and the host-side sequencing of one AGF2
 // iteration (moments -> compression -> Fock loop -> energies).  All array
-// arithmetic runs in this library's CUDA kernels (fp64.cu, mixed.cu) or in
-// cuSOLVER/cuBLAS for the O(N^3) FP64 dense linear algebra of the
-// compression and the extended-Hamiltonian eigendecomposition; the host only
-// takes scalar decisions (aufbau count, bisection bracket, DIIS
-// coefficients, convergence).
+// arithmetic runs in this library's CUDA kernels (fp64.cu, mixed.cu,
+// eigen.cu: the Fock loop's extended-Hamiltonian eigensolver) or in
+// cuSOLVER/cuBLAS for the small O(N^3) FP64 dense linear algebra of the
+// compression (Cholesky, triangular solves, the N x N or (m+1)N x (m+1)N
+// eigenproblem); the host only takes scalar decisions (aufbau count, shift
+// step or bracket, DIIS coefficients, convergence).
 #include <cublas_v2.h>
 #include <cusolverDn.h>
 #include <nvtx3/nvToolsExt.h>

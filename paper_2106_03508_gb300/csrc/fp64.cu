@@ -3,9 +3,12 @@
 // Fock build, the 2J-K / energy-weight epilogue, and the small kernels of the
 // compression / Fock loop / energy steps.
 //
-// GB300 executes FP64 at a small fraction of its BF16 tensor rate, so every
-// FP64 kernel here is bound by the FP64 pipe, not by memory: a register-tiled
-// SIMT tile (64x64x16, 4x4 per thread) is enough to keep that pipe busy.
+// GB300 executes FP64 at a small fraction of its BF16 tensor rate, so the
+// GEMMs here are bound by the FP64 pipe, not by memory: a register-tiled SIMT
+// tile (64x64 with 4x4 per thread, or 40x40 with 5x5 per thread where that
+// pads the output less) keeps the pipe ~95-99% busy once enough CTAs run
+// (split-K with FP64 atomics for long-K products, upper tiles only for
+// symmetric outputs).
 #include <algorithm>
 
 #include "agf2_internal.h"

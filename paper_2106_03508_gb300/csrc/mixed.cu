@@ -1,13 +1,14 @@
 // Split-precision moment build on the tcgen05 tensor cores (AGF2_BF16X3).
 //
-// The self-energy moments of Eqs. (mp2_zeroth_moment), (mp2_first_moment) are
-// evaluated over unordered pole pairs (x <= y) of the summed outer index
-// (i,j occupied for the hole sector; a,b virtual for the particle sector):
+// The self-energy moments of Eqs. (mp2_zeroth_moment), (mp2_first_moment)
+// and their higher analogues (weights w^n, n <= nmom <= 3) are evaluated over
+// unordered pole pairs (x <= y) of the summed outer index (i,j occupied for
+// the hole sector; a,b virtual for the particle sector):
 //
 //   X_xy[p,c] = sum_Q Lx[x][p][Q] Lpair[y][c][Q]        (GEMM 1, K = n_Q)
 //   S = X_xy + X_yx,  D = X_xy - X_yx,  w = e_x + e_y - e_c
-//   Y  = [ sqrt(cS) S | sqrt(cD) D ],  Yw = w Y
-//   U^(0) += Y Y^T,   U^(1) += Yw Y^T                    (GEMM 2, K = pairs x c)
+//   Y  = [ sqrt(cS) S | sqrt(cD) D ]
+//   U^(n) += (Y w^n) Y^T,  n = 0 .. nmom                 (GEMM 2, K = pairs x c)
 //
 // with (cS, cD) = (1/2, 3/2) for x < y and (1/4, 3/4) for x = y, which is
 // the pair-symmetrised form of sum_{xyc} X_xy (2 X_xy - X_yx) w^n (the
@@ -23,9 +24,12 @@
 // accumulator, which over long K biases a single accumulator by ~2^-25 per
 // instruction.  GEMM 2 drains its tiles into the FP64 moments.
 //
-// Kernels: split_limbs (FP64 -> limb planes), gemm6<PAIR> (GEMM 1 + the
-// S/D/weight epilogue, writing Y and Yw limb planes), gemm6<MOMENT> (GEMM 2,
-// split-K, FP64 reduction).
+// Kernels: slice_rows_kernel (FP64 rotated rows -> limb planes),
+// gemm6_kernel<MODE_PAIR> (GEMM 1, writing X in FP32 for a block of pairs),
+// combine_kernel<0/1> (S/D and energy weights; exact per-row maxima of
+// Y w^n, then fixed-point limb planes of every Y w^n),
+// gemm6_kernel<MODE_MOMENT> (GEMM 2 for every moment, upper tiles, split-K,
+// FP64 atomics), mirror_tiles_kernel (the lower tiles).
 #include <cuda.h>
 #include <cuda_bf16.h>
 #include <cudaTypedefs.h>
