@@ -364,3 +364,26 @@ def test_block_lanczos_resolvent_energy_converges_to_mp2():
         errs.append(abs(e2 - mp2))
     assert all(b < a for a, b in zip(errs, errs[1:])), errs
     assert errs[-1] < 1e-4 * abs(mp2), errs
+
+
+def test_compression_independent_of_the_factor_of_u0():
+    """The physical self-energy of the compressed auxiliaries does not depend
+    on which factor T of U^(0) = T T^T is used: with the symmetric square root
+    in place of the lower Cholesky factor, M' = T'^-1 U1 T'^-T is an orthogonal
+    similarity of M, so the auxiliary energies agree and so does
+    Sigma(w) = v (w - E)^-1 v^T at any w."""
+    s = make_system(10, 3, 30, 41)
+    e, C, mu = random_poles(10, 30, 11, 42)
+    Uh, Up = O.build_moments(s.L, e, C, mu)
+    for U in (Uh, Up):
+        E, v = O.compress(U[0], U[1])
+        lam, Z = np.linalg.eigh(U[0])
+        Ts = Z @ np.diag(np.sqrt(lam)) @ Z.T              # symmetric square root
+        Tinv = np.linalg.inv(Ts)
+        Es, W = np.linalg.eigh(Tinv @ U[1] @ Tinv.T)
+        vs = Ts @ W
+        assert np.max(np.abs(E - Es)) < 1e-10 * np.max(np.abs(E))
+        for w in (-7.3, 0.41, 5.9):
+            sig = (v / (w - E)) @ v.T
+            sig_s = (vs / (w - Es)) @ vs.T
+            assert rel(sig, sig_s) < 1e-9
