@@ -131,7 +131,7 @@ int agf2_compress_moments(agf2_handle h, const double* U, int nmo, int nmom, dou
  *   w [n]           out  eigenvalues, ascending
  *   V [n][n]        out  column-major: eigenvector x in V[x n .. x n + n),
  *                        of which only the first nphys entries are written
- * Returns AGF2_ERR_INVALID_ARG unless 1 <= nphys <= n <= 8000, and
+ * Returns AGF2_ERR_INVALID_ARG unless 1 <= nphys <= n <= 7000, and
  * AGF2_ERR_TIMEOUT if the tridiagonalisation's grid barrier gave up.
  */
 int agf2_eigh_physical(agf2_handle h, const double* A, int n, int nphys, double* w, double* V);

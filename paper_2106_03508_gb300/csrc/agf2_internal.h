@@ -119,7 +119,7 @@ int mixed_build_moments_rotated(const double* Lxo, const double* Lxv, const doub
                                 cudaStream_t s, KernelStats* stats, void* workspace);
 // Symmetric FP64 eigensolver (eigen.cu): eigenvalues ascending into w and
 // the first nphys rows of the eigenvectors into V (column-major, column x at
-// V + x n).  A [n][n] symmetric is not modified.  Workspace: one per handle.
+// V + x n), n <= 7000.  A [n][n] symmetric is not modified.  Workspace: one per handle.
 int eigh_phys(void* workspace, const double* A, int n, int nphys, double* w, double* V,
               cudaStream_t s, std::string& err);
 void* eig_workspace_create();

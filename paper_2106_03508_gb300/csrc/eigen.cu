@@ -956,8 +956,9 @@ void eig_workspace_destroy(void* p) {
 int eigh_phys(void* workspace, const double* Ain, int n, int nphys, double* w_out, double* V,
               cudaStream_t s, std::string& err) {
   EigWs& W = *static_cast<EigWs*>(workspace);
-  if (n < 1 || nphys < 1 || nphys > n || n > 8000) {
-    err = "eigh_phys: need 1 <= nphys <= n <= 8000";
+  // the tridiagonalisation keeps four length-n vectors in shared memory
+  if (n < 1 || nphys < 1 || nphys > n || n > 7000) {
+    err = "eigh_phys: need 1 <= nphys <= n <= 7000";
     return AGF2_ERR_INVALID_ARG;
   }
   const long long nn = (long long)n * n;
