@@ -125,3 +125,16 @@ def test_rejects_bad_sizes(cuda_handle, agf2_lib):
     with pytest.raises(agf2_lib.AGF2Error) as ei:
         eigh_gpu(agf2_lib, cuda_handle, A, nphys=5)
     assert ei.value.code == agf2_lib.AGF2_ERR_INVALID_ARG
+
+
+def test_extended_global_rows(cuda_handle, agf2_lib):
+    """n = 2000: too many rows per CTA for shared memory, so the
+    tridiagonalisation keeps them in global memory (the variant of
+    nmom = 3 at nmo = 500 and of nmo >= 1000)."""
+    A = extended(400, 1600, 33, dup=False)
+    w, C = eigh_gpu(agf2_lib, cuda_handle, A, nphys=400)
+    wr = np.linalg.eigvalsh(A)
+    scale = np.abs(wr).max()
+    assert np.abs(w - wr).max() <= 1e-11 * scale
+    assert np.abs(C @ C.T - np.eye(400)).max() <= 1e-10
+    assert np.abs((C * w) @ C.T - A[:400, :400]).max() <= 1e-10 * scale
