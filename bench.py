@@ -208,6 +208,40 @@ def peaks():
     return {"hbm_gbs": 6800.0, "bf16_tflops": 1900.0, "bf16_tflops_sustained": 1700.0}, "fallback"
 
 
+KERNEL_NAMES = {
+    0: "gemm6_kernel<PAIR> (split-BF16 tcgen05 GEMM 1 + S/D/weight epilogue)",
+    1: "gemm6_kernel<MOMENT> (split-BF16 tcgen05 GEMM 2 into U)",
+    2: "dgemm_kernel (FP64 DF Fock-build GEMMs: L D or L C, and K)",
+    3: "eigh_phys (FP64 extended-Hamiltonian eigensolver: sytrd_kernel + divide and conquer)",
+}
+
+
+def kernel_rooflines(k_stats, steps, pk, src):
+    """Roofline objects of the four timed kinds (agf2_kernel_stats: launches,
+    ms, algorithmic flops) and the dominant kind by device time.  The
+    tensor-core kinds 0, 1 are measured against the sustained BF16 peak, the
+    FP64 kinds 2, 3 against the nominal FP64 rate ("alu")."""
+    bf16_peak = pk.get("bf16_tflops_sustained", pk.get("bf16_tflops"))
+
+    def roof(kind):
+        n_k, ms_k, fl_k = k_stats[kind]
+        ach = fl_k / (ms_k / 1e3) / 1e12 if ms_k > 0 else 0.0
+        if kind in (0, 1):
+            return {"bound": "tensor", "kernel": KERNEL_NAMES[kind], "launches": n_k,
+                    "ms_per_step": ms_k / steps, "achieved": ach, "peak": bf16_peak,
+                    "unit": "TFLOP/s", "frac": ach / bf16_peak if bf16_peak else None,
+                    "issued_tflops": 6 * ach,
+                    "peak_source": f"bf16_tflops_sustained ({src}), of measured"}
+        return {"bound": "alu", "kernel": KERNEL_NAMES[kind], "launches": n_k,
+                "ms_per_step": ms_k / steps, "achieved": ach, "peak": FP64_NOMINAL_TFLOPS,
+                "unit": "TFLOP/s", "frac": ach / FP64_NOMINAL_TFLOPS,
+                "peak_source": "FP64 FMA pipe, nominal 1.25 TFLOP/s (no measured FP64 peak "
+                               "in MEASURED_PEAKS.json)"}
+
+    dominant = max((0, 1, 2, 3), key=lambda k: k_stats[k][1])
+    return dominant, {k: roof(k) for k in (0, 1, 2, 3)}
+
+
 def run_batched(args):
     """--config c4: 64 synthetic systems of uneven size (nmo ~ U[30,150],
     nocc = nmo/5, naux = 4 nmo, seeds 100-163) through agf2_run_batched; one
@@ -379,31 +413,7 @@ def run_ours(args):
         return
 
     pk, src = peaks()
-    # the dominant kernel of the step by measured device time: the tensor-core
-    # moment GEMMs (kinds 0, 1) against the FP64 Fock-build GEMMs (2) and the
-    # FP64 eigensolver (3) of the Fock loop
-    dominant = max((0, 1, 2, 3), key=lambda k: k_stats[k][1])
-    bf16_peak = pk.get("bf16_tflops_sustained", pk.get("bf16_tflops"))
-    fp64_peak = FP64_NOMINAL_TFLOPS
-    kname = {0: "gemm6_kernel<PAIR> (split-BF16 tcgen05 GEMM 1 + S/D/weight epilogue)",
-             1: "gemm6_kernel<MOMENT> (split-BF16 tcgen05 GEMM 2 into U)",
-             2: "dgemm_kernel (FP64 DF Fock-build GEMMs: L D or L C, and K)",
-             3: "eigh_phys (FP64 extended-Hamiltonian eigensolver: sytrd_kernel + divide and conquer)"}
-
-    def roof(kind):
-        n_k, ms_k, fl_k = k_stats[kind]
-        ach = fl_k / (ms_k / 1e3) / 1e12 if ms_k > 0 else 0.0
-        if kind in (0, 1):
-            return {"bound": "tensor", "kernel": kname[kind], "launches": n_k,
-                    "ms_per_step": ms_k / args.steps, "achieved": ach, "peak": bf16_peak,
-                    "unit": "TFLOP/s", "frac": ach / bf16_peak if bf16_peak else None,
-                    "issued_tflops": 6 * ach,
-                    "peak_source": f"bf16_tflops_sustained ({src}), of measured"}
-        return {"bound": "alu", "kernel": kname[kind], "launches": n_k,
-                "ms_per_step": ms_k / args.steps, "achieved": ach, "peak": fp64_peak,
-                "unit": "TFLOP/s", "frac": ach / fp64_peak,
-                "peak_source": "FP64 FMA pipe, nominal 1.25 TFLOP/s (no measured FP64 peak "
-                               "in MEASURED_PEAKS.json)"}
+    dominant, roofs = kernel_rooflines(k_stats, args.steps, pk, src)
 
     mom_t = statistics.mean(r["t_moments"] for r in results)
     mom_fl = statistics.mean(r["flops_moments"] for r in results)
@@ -420,11 +430,11 @@ def run_ours(args):
                                    for k in ("t_moments", "t_compress", "t_fock", "t_energy")},
         "moment_build": {"tflops_algorithmic": mom_fl / mom_t / 1e12, "flops_per_iter": mom_fl,
                          "seconds": mom_t},
-        "roofline": {**roof(dominant), "traffic": NCU_TRAFFIC.get((args.config, dominant)),
+        "roofline": {**roofs[dominant], "traffic": NCU_TRAFFIC.get((args.config, dominant)),
                      "note": "dominant kernel of the step by device time; achieved = algorithmic "
                              "flops / CUDA-event time (the split-BF16 kernels issue 6 limb "
                              "products per algorithmic product)"},
-        "kernels": {str(k): roof(k) for k in (0, 1, 2, 3)},
+        "kernels": {str(k): roofs[k] for k in (0, 1, 2, 3)},
         "gpu_launches": launches,
         "clocks": clocks,
         "e2e": e2e,

@@ -1,0 +1,33 @@
+"""Host logic of bench.py that needs no GPU: the roofline objects built from
+the library's per-kind timing stats, and the steady-state pole counts the
+CPU baseline extrapolates to."""
+import bench
+
+
+def test_dominant_kernel_and_rooflines():
+    peaks = {"bf16_tflops": 1900.0, "bf16_tflops_sustained": 1700.0}
+    # kind: (launches, ms, algorithmic flops) over 5 steps
+    stats = {0: (100, 400.0, 6.8e13), 1: (100, 300.0, 2.55e13),
+             2: (500, 9000.0, 9.0e15), 3: (500, 5500.0, 2.9e14)}
+    dom, roofs = bench.kernel_rooflines(stats, 5, peaks, "measured")
+    assert dom == 2
+    r = roofs[2]
+    assert r["bound"] == "alu" and r["peak"] == bench.FP64_NOMINAL_TFLOPS
+    assert abs(r["achieved"] - 9.0e15 / 9.0 / 1e12) < 1e-9
+    assert abs(r["frac"] - r["achieved"] / 1.25) < 1e-12
+    assert abs(r["ms_per_step"] - 1800.0) < 1e-9
+    t = roofs[0]
+    assert t["bound"] == "tensor" and t["peak"] == 1700.0
+    assert abs(t["achieved"] - 170.0) < 1e-9 and abs(t["issued_tflops"] - 1020.0) < 1e-9
+    # nothing timed: zero rates, no division by zero
+    dom0, roofs0 = bench.kernel_rooflines({k: (0, 0.0, 0.0) for k in range(4)}, 1, peaks, "m")
+    assert all(roofs0[k]["achieved"] == 0.0 for k in range(4))
+
+
+def test_steady_state_pole_counts():
+    from paper_2106_03508_gb300.synth import CONFIGS
+    for nmom in (1, 3):
+        s, o, v = bench._oracle_setup("c1", nmom)
+        N = CONFIGS["c1"]["nmo"]
+        assert o + v == (nmom + 2) * N
+        assert o == CONFIGS["c1"]["nocc"] + (nmom + 1) // 2 * N
