@@ -15,14 +15,19 @@ in order:
   (particle) sector          ``build_moments`` (per-i / per-a GEMM form) and
                              ``build_moments_loops`` (explicit sums, tiny N)
 * Eq. (block_lanczos_chol_3) and the M-block that follows it
-                              ``compress``
+                              ``compress``; the higher truncations of the
+                              compression paragraph (moments 0..2m+1, m+1
+                              block-Lanczos steps from the moments)
+                              ``compress_block_lanczos``
 * Eq. (post_compression_h) / (dyson_eq_eig)
                               ``diagonalise``
 * the density relaxation with a chemical potential keeping the electron count
   in the non-idempotent density (text after Eq. dyson_eq_eig)
                               ``aufbau``, ``solve_shift``, ``fock_loop``
 * energies / IP / EA          ``energies``
-* the outer self-consistency  ``run``
+* the outer self-consistency  ``run`` (any odd nmom)
+* the broadened spectral function of the artemisinin figures
+                              ``spectral_function``
 
 Readings taken where the paper is silent (identical on the CUDA side):
   - occupied poles are those with e < mu (a pole exactly at mu is virtual);
@@ -39,9 +44,11 @@ Readings taken where the paper is silent (identical on the CUDA side):
 
 Parity is pinned (tests/test_oracle.py) by brute-force four-index sums, the
 MP2 closed form at the HF reference, the S/D factorisation of the exact
-uncompressed self-energy, homogeneity, the compression identities,
-completeness of the extended eigenvectors, electron-count conservation and
-the weak-coupling limit.  The converged IP/EA/E_tot of the full iteration are
+uncompressed self-energy, homogeneity, the compression identities (and
+their independence from the factor of U^(0)), the block-Lanczos moment
+conservation and its MP2 limit, completeness of the extended eigenvectors,
+electron-count conservation, the spectral sum rule and the weak-coupling
+limit.  The converged IP/EA/E_tot of the full iteration are
 parity unpinned beyond these invariants (the paper's numbers need molecular
 data).
 """
