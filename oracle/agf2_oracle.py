@@ -24,7 +24,7 @@ in order:
 * the density relaxation with a chemical potential keeping the electron count
   in the non-idempotent density (text after Eq. dyson_eq_eig)
                               ``aufbau``, ``solve_shift``, ``fock_loop``
-* energies / IP / EA          ``energies``
+* energies / IP / EA          ``energy_1body``, ``energy_2body`` (IP/EA in ``run``)
 * the outer self-consistency  ``run`` (any odd nmom)
 * the broadened spectral function of the artemisinin figures
                               ``spectral_function``
