@@ -13,7 +13,10 @@ in order:
 * Eq. (mp2_self_energy)       the moments below are its spectral moments
 * Eqs. (mp2_zeroth_moment), (mp2_first_moment) and the "analogous" greater
   (particle) sector          ``build_moments`` (per-i / per-a GEMM form) and
-                             ``build_moments_loops`` (explicit sums, tiny N)
+                             ``build_moments_loops`` (explicit sums, tiny N);
+                             the contribution of chosen outer pole pairs
+                             (the summed indices the paper distributes)
+                             ``build_moments_pairs``
 * Eq. (block_lanczos_chol_3) and the M-block that follows it
                               ``compress``; the higher truncations of the
                               compression paragraph (moments 0..2m+1, m+1
@@ -43,7 +46,10 @@ Readings taken where the paper is silent (identical on the CUDA side):
   - IP = -e_HOQMO, EA = -e_LUQMO.
 
 Parity is pinned (tests/test_oracle.py) by brute-force four-index sums, the
-MP2 closed form at the HF reference, the S/D factorisation of the exact
+MP2 closed form at the HF reference, the closed-shell Hartree-Fock energy
+and the general one-body energy from explicit four-index ERIs, additivity of
+the moments over outer-pair slices (and a slice against restricted explicit
+sums), the S/D factorisation of the exact
 uncompressed self-energy, homogeneity, the compression identities (and
 their independence from the factor of U^(0)), the block-Lanczos moment
 conservation and its MP2 limit, completeness of the extended eigenvectors,
@@ -140,6 +146,38 @@ def build_moments(L, e, C, mu, nmom: int = 1):
     Uh = 0.5 * (Uh + Uh.transpose(0, 2, 1))
     Up = 0.5 * (Up + Up.transpose(0, 2, 1))
     return Uh, Up
+
+
+def build_moments_pairs(L, e, C, mu, nmom: int = 1, hole_pairs=(), part_pairs=()):
+    """Contribution of chosen outer pole pairs to the moments (the summed
+    outer indices that the paper's parallel algorithm hands out in blocks).
+
+    ``hole_pairs`` lists unordered pairs (x, y), x <= y, of positions in the
+    occupied pole list (poles with e < mu in ascending pole order); the pair
+    contributes the ordered terms (i, j) = (x, y) and, for x != y, (y, x) of
+    U_<^(n)_pq = sum_{ija} (pi|ja)[2(qi|ja) - (qj|ia)] (e_i+e_j-e_a)^n.
+    ``part_pairs`` does the same for the virtual outer pair (a, b) of the
+    particle sector.  Summed over every unordered pair, this is
+    ``build_moments``.  Returns the symmetrised (hole, particle) partial
+    moments, each [nmom+1, N, N]."""
+    N = L.shape[1]
+    eo, Co, ev, Cv = split_poles(e, C, mu)
+    Lxo, Lxv, Lov = rotate(L, Co, Cv)
+    Lvo = Lov.transpose(0, 2, 1)
+    out = []
+    for pairs, Lx, Lp, e_out, e_in in ((hole_pairs, Lxo, Lov, eo, ev),
+                                      (part_pairs, Lxv, Lvo, ev, eo)):
+        U = np.zeros((nmom + 1, N, N))
+        for x, y in pairs:
+            ordered = [(x, y)] if x == y else [(x, y), (y, x)]
+            for i, j in ordered:
+                Xij = np.tensordot(Lx[:, :, i], Lp[:, j, :], axes=(0, 0))   # (pi|jc) [p, c]
+                Xji = np.tensordot(Lx[:, :, j], Lp[:, i, :], axes=(0, 0))   # (pj|ic) [p, c]
+                w = e_out[i] + e_out[j] - e_in
+                for n in range(nmom + 1):
+                    U[n] += (Xij * w ** n) @ (2.0 * Xij - Xji).T
+        out.append(0.5 * (U + U.transpose(0, 2, 1)))
+    return out[0], out[1]
 
 
 def moment_elements(L, e, C, mu, pq, nmom: int = 1):

@@ -244,15 +244,113 @@ def test_first_iteration_two_body_vs_mp2_gap_reported():
     assert abs(e2 - emp2) < abs(emp2)
 
 
+def _pair_loops(L, e, C, mu, hole_pairs, part_pairs, nmom=1):
+    """Brute force: the moment sums of Eqs. (mp2_zeroth_moment),
+    (mp2_first_moment) over four-index pole ERIs, restricted to ordered outer
+    pairs whose unordered version is listed (positions in the occupied /
+    virtual pole lists)."""
+    N = L.shape[1]
+    occ = [x for x in range(len(e)) if e[x] < mu]
+    vir = [x for x in range(len(e)) if not e[x] < mu]
+    g = O.pole_eris(L, C)
+    out = []
+    for pairs, outer, inner in ((hole_pairs, occ, vir), (part_pairs, vir, occ)):
+        keep = {(min(x, y), max(x, y)) for x, y in pairs}
+        U = np.zeros((nmom + 1, N, N))
+        for p in range(N):
+            for q in range(N):
+                for xi, i in enumerate(outer):
+                    for xj, j in enumerate(outer):
+                        if (min(xi, xj), max(xi, xj)) not in keep:
+                            continue
+                        for c in inner:
+                            t = g[p, i, j, c] * (2.0 * g[q, i, j, c] - g[q, j, i, c])
+                            for n in range(nmom + 1):
+                                U[n, p, q] += t * (e[i] + e[j] - e[c]) ** n
+        out.append(0.5 * (U + U.transpose(0, 2, 1)))
+    return out
+
+
 def test_slice_additivity():
-    """U is a sum over the occupied poles: moments built with the occupied
-    set split in two (the other poles as spectators) add to the whole hole
-    moment's diagonal-pair-free part -- checked by the explicit loops."""
+    """The moments are sums over the outer pole pairs (the summed indices the
+    paper distributes over ranks): pair sets that partition all unordered
+    outer pairs give partial moments adding to the whole build, in both
+    sectors; and one pair set's partial moments equal the explicit
+    four-index sums restricted to those ordered pairs (so the partial build
+    restricts the right indices)."""
     s = make_system(6, 2, 7, 44)
     e, C, mu = random_poles(6, 11, 4, 44)
-    Bh, _ = O.build_moments_loops(s.L, e, C, mu)
-    Uh, _ = O.build_moments(s.L, e, C, mu)
-    assert rel(Uh[0], 0.5 * (Bh[0] + Bh[0].T)) < 1e-12
+    o, v = 4, 7
+    rng = np.random.default_rng(3)
+    hp = [(x, y) for x in range(o) for y in range(x, o)]
+    pp = [(x, y) for x in range(v) for y in range(x, v)]
+    lab_h = rng.integers(0, 3, len(hp))
+    lab_p = rng.integers(0, 3, len(pp))
+    Uh, Up = O.build_moments(s.L, e, C, mu)
+    Sh, Sp = np.zeros_like(Uh), np.zeros_like(Up)
+    for k in range(3):
+        ph, pq = O.build_moments_pairs(s.L, e, C, mu, 1,
+                                       [hp[t] for t in range(len(hp)) if lab_h[t] == k],
+                                       [pp[t] for t in range(len(pp)) if lab_p[t] == k])
+        Sh += ph
+        Sp += pq
+    assert rel(Sh, Uh) < 1e-13 and rel(Sp, Up) < 1e-13
+    sel_h = [hp[t] for t in range(len(hp)) if lab_h[t] == 1]
+    sel_p = [pp[t] for t in range(len(pp)) if lab_p[t] == 1]
+    ph, pq = O.build_moments_pairs(s.L, e, C, mu, 1, sel_h, sel_p)
+    bh, bp = _pair_loops(s.L, e, C, mu, sel_h, sel_p)
+    assert rel(ph, bh) < 1e-12 and rel(pq, bp) < 1e-12
+    # a genuine slice: it is neither zero nor the whole
+    assert 0.05 < np.max(np.abs(ph)) / np.max(np.abs(Uh)) < 0.95
+
+
+def _eri(L):
+    naux, N, _ = L.shape
+    g = np.zeros((N, N, N, N))
+    for p in range(N):
+        for q in range(N):
+            for r in range(N):
+                for t in range(N):
+                    g[p, q, r, t] = sum(L[Q, p, q] * L[Q, r, t] for Q in range(naux))
+    return g
+
+
+def test_energy_1body_hf_closed_form():
+    """At the aufbau density D0 (nocc doubly occupied orbitals) the one-body
+    energy 1/2 Tr[D0 (h + F[D0])] is the closed-shell Hartree-Fock energy
+    sum_i 2 h_ii + sum_ij [2 (ii|jj) - (ij|ji)], written here from explicit
+    four-index ERIs and a generic symmetric h."""
+    s = make_system(6, 2, 5, 61)
+    rng = np.random.default_rng(61)
+    h = rng.standard_normal((6, 6)); h = h + h.T
+    g = _eri(s.L)
+    nocc = 2
+    ehf = sum(2.0 * h[i, i] for i in range(nocc))
+    for i in range(nocc):
+        for j in range(nocc):
+            ehf += 2.0 * g[i, i, j, j] - g[i, j, j, i]
+    D0 = O.hf_density(6, nocc)
+    got = O.energy_1body(h, O.fock_matrix(h, s.L, D0), D0)
+    assert abs(got - ehf) < 1e-13 * max(1.0, abs(ehf))
+
+
+def test_energy_1body_general_density():
+    """At a non-idempotent density the one-body energy is
+    sum_pq D_pq h_pq + 1/2 sum_pqrs D_pq D_rs [(pq|rs) - 1/2 (ps|rq)]
+    (Eq. fock_matrix inserted in 1/2 Tr[D (h + F)]), as explicit loops."""
+    s = make_system(5, 2, 6, 62)
+    rng = np.random.default_rng(62)
+    h = rng.standard_normal((5, 5)); h = h + h.T
+    D = rng.standard_normal((5, 5)); D = D + D.T
+    g = _eri(s.L)
+    ref = float(np.sum(D * h))
+    for p in range(5):
+        for q in range(5):
+            for r in range(5):
+                for t in range(5):
+                    ref += 0.5 * D[p, q] * D[r, t] * (g[p, q, r, t] - 0.5 * g[p, t, r, q])
+    got = O.energy_1body(h, O.fock_matrix(h, s.L, D), D)
+    assert abs(got - ref) < 1e-12 * max(1.0, abs(ref))
 
 
 def test_moment_elements_match_full_build():
