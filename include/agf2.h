@@ -178,7 +178,8 @@ void agf2_fock_opts_default(agf2_fock_opts* o);
  *   e_qmo [nmo+nse]         out     poles, ascending
  *   C_qmo [nmo][nmo+nse]    out     physical part of the eigenvectors
  *   opts  host pointer or NULL (defaults); info host pointer or NULL
- * Returns AGF2_ERR_NO_CONVERGENCE (outputs valid) if the cap is reached.
+ * Returns AGF2_ERR_NO_CONVERGENCE (outputs valid) if the cap is reached,
+ * AGF2_ERR_INVALID_ARG if nmo + nse > 7000 (the eigensolver's limit).
  */
 int agf2_fock_loop(agf2_handle h, const double* hcore, const double* L, int naux,
                    int nmo, int nelec, double* E_se, const double* v_se, int nse,
@@ -224,7 +225,8 @@ void agf2_opts_default(agf2_opts* o);
  *   hcore [nmo][nmo], L [naux][nmo][nmo], eps0 [nmo]: device pointers
  *   opts, out: host pointers (opts NULL = defaults)
  * Returns AGF2_ERR_NO_CONVERGENCE (with *out filled) if max_iter is reached
- * before convergence and max_iter > 1.
+ * before convergence and max_iter > 1, AGF2_ERR_INVALID_ARG if the extended
+ * Hamiltonian would exceed the eigensolver's limit, nmo (nmom + 2) > 7000.
  */
 int agf2_run(agf2_handle h, const double* hcore, const double* L, int naux, int nmo,
              int nelec, const double* eps0, const agf2_opts* opts, agf2_result* out);
@@ -300,11 +302,12 @@ int agf2_kernel_stats(agf2_handle h, int kind, long long* launches, double* ms, 
  * would synchronise the device and a late cudaMalloc could fail.  It needs no
  * handle and calls no cudaMalloc/cudaFree: every intermediate lives in one
  * static device array of 64 MiB inside the library, held on every GPU that
- * loads the library until the process exits.  Roughly, the intermediates take
- * 8 (nqmo nmo naux + o' v' naux + 6 nmo max(o', v')) bytes (o', v': occupied
- * and virtual pole counts); sizes that could exceed 64 MiB for any
- * occupied/virtual split are rejected with AGF2_ERR_INVALID_ARG before any
- * argument is read.
+ * loads the library until the process exits.  The intermediates take
+ * 8 (nqmo nmo naux + o' v' naux + 6 nmo max(o', v')) bytes plus O(nqmo nmo)
+ * (o', v': occupied and virtual pole counts); the call takes the largest of
+ * this over every split o' + v' = nqmo and rejects sizes where it exceeds
+ * 64 MiB with AGF2_ERR_INVALID_ARG before any argument is read, so an
+ * accepted size fits whatever the pole energies are.
  *   Arguments and outputs as agf2_build_moments (nmom = 1); `stream` is a
  *   cudaStream_t passed as void* (NULL: legacy default stream).  Returns when
  *   the outputs are complete.

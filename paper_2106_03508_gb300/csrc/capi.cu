@@ -1112,6 +1112,8 @@ int agf2_fock_loop(agf2_handle h, const double* hcore, const double* L, int naux
   int rc = guarded(h, [&](agf2_context* ctx) {
     if (naux < 1 || nmo < 1 || nse < 0 || nelec < 1 || nelec > 2 * (nmo + nse))
       fail(ctx, AGF2_ERR_INVALID_ARG, "bad sizes");
+    if (nmo + nse > 7000)
+      fail(ctx, AGF2_ERR_INVALID_ARG, "nmo + nse > 7000: beyond the extended-Hamiltonian eigensolver");
     for (auto p : {(const void*)hcore, (const void*)L, (const void*)E_se, (const void*)v_se,
                    (const void*)D, (const void*)F, (const void*)e_qmo, (const void*)C_qmo})
       check_dev_ptr(ctx, p, "argument");
@@ -1147,6 +1149,9 @@ int agf2_run(agf2_handle h, const double* hcore, const double* L, int naux, int 
       fail(ctx, AGF2_ERR_INVALID_ARG, "nmom must be odd (AGF2(m,0) uses nmom = 2m+1)");
     if (o.precision == AGF2_BF16X3 && o.nmom > 3)
       fail(ctx, AGF2_ERR_UNSUPPORTED, "AGF2_BF16X3 supports nmom <= 3");
+    if ((long long)nmo * (o.nmom + 2) > 7000)
+      fail(ctx, AGF2_ERR_INVALID_ARG,
+           "nmo (nmom + 2) > 7000: beyond the extended-Hamiltonian eigensolver");
     check_dev_ptr(ctx, hcore, "hcore");
     check_dev_ptr(ctx, L, "L");
     cudaStream_t s = ctx->stream;

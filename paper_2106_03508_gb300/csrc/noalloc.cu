@@ -69,15 +69,36 @@ struct Arena {
   }
 };
 
-size_t pad(size_t bytes) { return (bytes + 255) / 256 * 256; }
+// Bytes the call can need for an occupied/virtual split o + v = nq, without
+// the 256-byte rounding of each piece: the gathered couplings and energies,
+// the three rotated tensors, and the smallest pair block (one outer pole per
+// block: X_IJ, X_JI, Y, Yw of 6 N max(o, v) doubles).  128-bit arithmetic,
+// so no size product can wrap.
+using u128 = unsigned __int128;
+u128 bytes_unpadded(u128 N, u128 nq, u128 o, u128 Q) {
+  const u128 v = nq - o;
+  return 4 * nq + 8 * N * nq + 8 * nq + 8 * N * Q * nq + 8 * Q * o * v +
+         48 * N * (o > v ? o : v);
+}
+constexpr int kPieces = 12;  // Arena::take calls per call; each rounds up by < 256 bytes
 
-// Bytes needed for o occupied / v virtual poles with pair blocks of one pole.
-size_t bytes_needed(size_t N, size_t nq, size_t o, size_t v, size_t naux) {
-  const size_t fixed = pad(nq * sizeof(int)) + pad(N * o * 8) + pad(N * v * 8) + pad(o * 8) +
-                       pad(v * 8) + pad(o * N * naux * 8) + pad(v * N * naux * 8) +
-                       pad(o * v * naux * 8);
-  const size_t block = 6 * N * std::max(o, v) * 8 + 4 * 256;
-  return fixed + block;
+// Largest need over every split 1 <= o <= nq - 1.  The need is symmetric
+// under o <-> nq - o; for o >= nq/2 it is 8 Q o (nq - o) + 48 N o plus
+// constants, a concave parabola with its vertex at o* = nq/2 + 3 N / Q, so
+// the maximum over the integers lies at floor(o*) or ceil(o*) clamped to
+// [ceil(nq/2), nq - 1].
+u128 worst_case_bytes(size_t N, size_t nq, size_t Q) {
+  const size_t half = (nq + 1) / 2;
+  const double vertex = 0.5 * (double)nq + 3.0 * (double)N / (double)Q;
+  u128 worst = 0;
+  const double cands[4] = {(double)half, (double)(nq - 1), std::floor(vertex),
+                           std::ceil(vertex)};
+  for (double c : cands) {
+    const double cl = std::min<double>(std::max<double>(c, (double)half), (double)(nq - 1));
+    const u128 b = bytes_unpadded(N, nq, (u128)cl, Q);
+    if (b > worst) worst = b;
+  }
+  return worst + (u128)kPieces * 256;
 }
 
 }  // namespace
@@ -91,12 +112,7 @@ extern "C" int agf2_build_moments_noalloc(const double* L, int naux, int nmo, co
     return AGF2_ERR_INVALID_ARG;
   const size_t N = nmo, nq = nqmo, Q = naux;
   // Size check before touching any argument: the worst split of nq poles.
-  {
-    size_t worst = 0;
-    for (size_t o : {size_t(1), nq / 2, nq - 1})
-      worst = std::max(worst, bytes_needed(N, nq, o, nq - o, Q));
-    if (worst > kScratchBytes) return AGF2_ERR_INVALID_ARG;
-  }
+  if (worst_case_bytes(N, nq, Q) > (u128)kScratchBytes) return AGF2_ERR_INVALID_ARG;
   cudaStream_t s = static_cast<cudaStream_t>(stream);
   void* sp = nullptr;
   if (int rc = scratch_address(&sp)) return rc;
@@ -167,11 +183,15 @@ extern "C" int agf2_build_moments_noalloc(const double* L, int naux, int nmo, co
     g.nb1 = (int)Q;
     NA_CK(agf2::dgemm(g, s));
   }
-  // Pair blocks sized to what is left of the array.
-  const size_t left_doubles = (A.cap - A.used) / 8 - 4 * 32;
+  // Pair blocks sized to what is left of the array (at least one outer pole
+  // per block fits: the size check above covers the worst split).
   const int n_in_max = std::max(o, v);
+  const size_t min_block = 48 * N * (size_t)n_in_max + 4 * 256;
+  if (A.used > A.cap || A.cap - A.used < min_block) return AGF2_ERR_INVALID_ARG;
+  const size_t left_doubles = (A.cap - A.used - 4 * 256) / 8;
   int nb = (int)std::floor(std::sqrt((double)left_doubles / (6.0 * N * n_in_max)));
   nb = std::max(1, nb);
+  while (nb > 1 && 6 * N * (size_t)nb * nb * n_in_max > left_doubles) --nb;
   const size_t K1max = (size_t)nb * nb * n_in_max;
   double* XIJ = A.take<double>(N * K1max);
   double* XJI = A.take<double>(N * K1max);

@@ -138,3 +138,22 @@ def test_extended_global_rows(cuda_handle, agf2_lib):
     assert np.abs(w - wr).max() <= 1e-11 * scale
     assert np.abs(C @ C.T - np.eye(400)).max() <= 1e-10
     assert np.abs((C * w) @ C.T - A[:400, :400]).max() <= 1e-10 * scale
+
+
+def test_extended_c5_shape_one_reflector_back_transformation(cuda_handle, agf2_lib):
+    """n = 3000 with 1000 physical rows (nmo = 1000, AGF2(1,0)): the
+    back-transformation's rows plus a block of eight reflectors exceed the
+    shared memory of one CTA, so the physical rows are formed one reflector at
+    a time (phys_rows_kernel) -- the path of every Fock cycle at nmo = 1000."""
+    A = extended(1000, 2000, 35, dup=True)
+    w, C = eigh_gpu(agf2_lib, cuda_handle, A, nphys=1000)
+    wr, Vr = np.linalg.eigh(A)
+    scale = np.abs(wr).max()
+    assert np.abs(w - wr).max() <= 1e-11 * scale
+    assert np.abs(C @ C.T - np.eye(1000)).max() <= 1e-10
+    assert np.abs((C * w) @ C.T - A[:1000, :1000]).max() <= 1e-10 * scale
+    gaps = np.nonzero(np.diff(wr) > 1e-6 * scale)[0] + 1
+    for k in gaps[:: max(1, len(gaps) // 10)]:
+        P = C[:, :k] @ C[:, :k].T
+        Pr = Vr[:1000, :k] @ Vr[:1000, :k].T
+        assert np.abs(P - Pr).max() <= 1e-9, k

@@ -130,33 +130,35 @@ def test_fock_loop_vs_oracle(cuda_handle, agf2_lib, shift_mode):
     E = np.sort(np.concatenate([rng.uniform(-4, -1, 16), rng.uniform(1, 5, 16)]))
     v = 0.3 * rng.standard_normal((16, nse))
     D0 = O.hf_density(16, 4)
-    ref = O.fock_loop(h, s.L, s.nelec, E, v, D0)
+    ref = O.fock_loop(h, s.L, s.nelec, E, v, D0, tol_D=1e-12)
     hd, Ld, Ed, vd, Dd = dev(h), dev(s.L), dev(E), dev(v), dev(D0)
     F, eq, Cq = empty(16, 16), empty(16 + nse), empty(16, 16 + nse)
     opts = agf2_lib.agf2_fock_opts_default()
     opts.shift_mode = shift_mode
     opts.max_cycle = 300
+    opts.tol_D = 1e-12
     rc, info = agf2_lib.agf2_fock_loop(cuda_handle.h, hd.data_ptr(), Ld.data_ptr(), s.naux, 16,
                                        s.nelec, Ed.data_ptr(), vd.data_ptr(), nse, Dd.data_ptr(),
                                        F.data_ptr(), eq.data_ptr(), Cq.data_ptr(), opts)
     assert ref.converged and info.converged
     assert info.nocc_qmo == ref.nocc_qmo
-    assert abs(info.mu - ref.mu) < 1e-9
-    assert rel(host(Dd), ref.D) < 1e-9
-    assert rel(host(F), ref.F) < 1e-9
-    assert rel(host(eq), ref.e) < 1e-9
-    assert rel(host(Ed), ref.E_shift) < 1e-9
+    assert abs(info.mu - ref.mu) < 1e-10 * abs(ref.mu)
+    assert rel(host(Dd), ref.D) < 1e-10
+    assert rel(host(F), ref.F) < 1e-10
+    assert rel(host(eq), ref.e) < 1e-10
+    assert rel(host(Ed), ref.E_shift) < 1e-10
     Cg = host(Cq)
     k = ref.nocc_qmo
     assert abs(2 * np.sum(Cg[:, :k] ** 2) - s.nelec) < 1e-9
 
 
-def run_gpu(lib, h, s, hcore, max_iter, precision=0, resume=0):
+def run_gpu(lib, h, s, hcore, max_iter, precision=0, resume=0, tol_D=1e-10):
     L, hc, eps = dev(s.L), dev(hcore), dev(s.eps)
     o = lib.agf2_opts_default()
     o.max_iter = max_iter
     o.precision = precision
     o.resume = resume
+    o.fock.tol_D = tol_D
     rc, out = lib.agf2_run(h.h, hc.data_ptr(), L.data_ptr(), s.naux, s.nmo, s.nelec,
                            eps.data_ptr(), o)
     return out
@@ -168,10 +170,12 @@ def test_run_small_vs_oracle(cuda_handle, agf2_lib):
     s = make_system(12, 3, 30, 8)
     s.L *= 0.5
     h = O.hcore_from_mo_energies(s.eps, s.L, s.nocc)
-    ref = O.run(h, s.L, s.nelec, s.eps, max_iter=30)
-    out = run_gpu(agf2_lib, cuda_handle, s, h, 30)
+    # both Fock loops converge the density to 1e-12, so that their fixed points
+    # agree well below the relative 1e-10 asserted on the energies
+    ref = O.run(h, s.L, s.nelec, s.eps, max_iter=30, fock_tol=1e-12)
+    out = run_gpu(agf2_lib, cuda_handle, s, h, 30, tol_D=1e-12)
     assert out.iterations == ref.iterations
     assert out.converged == int(ref.converged)
     for a, b in ((out.E_hf, ref.E_hf), (out.E_tot, ref.E_tot), (out.E_1b, ref.E_1b),
                  (out.E_2b, ref.E_2b), (out.ip, ref.ip), (out.ea, ref.ea)):
-        assert abs(a - b) <= 1e-9 * abs(b), (a, b)
+        assert abs(a - b) <= 1e-10 * abs(b), (a, b)

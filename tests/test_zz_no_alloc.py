@@ -1,13 +1,15 @@
 """The allocation-free FP64 moment build (agf2_build_moments_noalloc) -- for
 callers whose own allocator owns the device memory budget and who cannot let
 a library call cudaMalloc/cudaFree -- must give what the regular
-agf2_build_moments gives, call after call, through the C ABI.
+agf2_build_moments gives, call after call, through the C ABI, and what the
+FP64 oracle gives.
 
 This file is collected last so that a stop-at-first-failure run has already
 run every other test; it also passes when run alone."""
 import numpy as np
 import pytest
 
+from oracle import agf2_oracle as O
 from paper_2106_03508_gb300.synth import make_system, random_poles
 
 pytestmark = pytest.mark.gpu
@@ -39,8 +41,48 @@ def test_noalloc_matches_regular_entry_point_twice(cuda_handle, agf2_lib):
         e, C, mu = random_poles(nmo, nq, no, seed + 3)
         Ah, Ap = _moments(agf2_lib, cuda_handle, s, e, C, mu, noalloc=True)
         Bh, Bp = _moments(agf2_lib, cuda_handle, s, e, C, mu, noalloc=False)
-        for a, b in ((Ah, Bh), (Ap, Bp)):
+        Rh, Rp = O.build_moments(s.L, e, C, mu)
+        for a, b, r in ((Ah, Bh, Rh), (Ap, Bp, Rp)):
             assert np.max(np.abs(a - b)) <= RTOL * np.max(np.abs(b))
+            assert np.max(np.abs(a - r)) <= RTOL * np.max(np.abs(r))
+
+
+def test_noalloc_at_the_size_limit(cuda_handle, agf2_lib):
+    """naux < nmo, where the largest need over the occupied/virtual splits
+    lies inside the range (o' = nqmo/2 + 3 nmo/naux): the largest accepted
+    pole count runs with that worst split and matches the oracle; one pole
+    more is rejected."""
+    import torch
+    nmo, naux = 512, 240
+    s = make_system(nmo, 100, naux, 12)
+    L = torch.from_numpy(s.L).cuda()
+    big = 256
+    U = torch.empty(2, 2, nmo, nmo, dtype=torch.float64, device="cuda")
+
+    def call(nq):
+        o = min(nq - 1, max(1, int(round(nq / 2 + 3 * nmo / naux))))
+        e, C, mu = random_poles(nmo, nq, o, nq)
+        ed, Cd = torch.from_numpy(e).cuda(), torch.from_numpy(C).cuda()
+        rc = agf2_lib.agf2_build_moments_noalloc(L.data_ptr(), naux, nmo, ed.data_ptr(),
+                                                 Cd.data_ptr(), nq, mu, U[0].data_ptr(),
+                                                 U[1].data_ptr(), 0)
+        torch.cuda.synchronize()
+        return rc, (e, C, mu)
+
+    lo, hi = 2, big          # call(lo) accepted, call(hi) rejected
+    assert call(lo)[0] == agf2_lib.AGF2_OK and call(hi)[0] == agf2_lib.AGF2_ERR_INVALID_ARG
+    while hi - lo > 1:
+        mid = (lo + hi) // 2
+        if call(mid)[0] == agf2_lib.AGF2_OK:
+            lo = mid
+        else:
+            hi = mid
+    rc, (e, C, mu) = call(lo)
+    assert rc == agf2_lib.AGF2_OK and lo > 16
+    Uh, Up = U[0].cpu().numpy(), U[1].cpu().numpy()
+    Rh, Rp = O.build_moments(s.L, e, C, mu)
+    for a, r in ((Uh, Rh), (Up, Rp)):
+        assert np.max(np.abs(a - r)) <= RTOL * np.max(np.abs(r))
 
 
 def test_noalloc_rejects_oversized_problem(agf2_lib):
