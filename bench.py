@@ -47,8 +47,6 @@ def parse():
     ap.add_argument("--precision", default="bf16x3", choices=["bf16x3", "fp64"])
     ap.add_argument("--fp64-steps", type=int, default=1,
                     help="FP64-path iterations timed after the main steps (0: skip)")
-    ap.add_argument("--cpu-seconds", type=float, default=15.0,
-                    help="target CPU time of the oracle sample")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--shift-mode", type=int, default=1, choices=[0, 1],
                     help="Fock-loop shift: 0 solve every cycle, 1 one Newton step per cycle")
@@ -70,6 +68,10 @@ def workload_desc(cfg, nmom=1):
 # ---------------------------------------------------------------------------
 # CPU oracle sample (cpu_baseline and --impl reference)
 # ---------------------------------------------------------------------------
+FOCK_CAP = 100                 # agf2_fock_opts default max_cycle (reached by the c2/c3 loops)
+ORACLE_FRACTION = 1.0 / 60.0   # share of the outer summed indices timed per sample
+
+
 def _oracle_setup(cfg, nmom=1):
     """Steady-state pole counts: nmo + (nmom+1) nmo poles, of which the nocc
     occupied orbitals' poles and the (nmom+1)/2 nmo hole auxiliaries' poles
@@ -82,39 +84,53 @@ def _oracle_setup(cfg, nmom=1):
     return s, o_full, (nmom + 2) * N - o_full
 
 
-def oracle_time(cfg, k, nmom=1):
-    """Seconds per full iteration extrapolated from one timed FP64-oracle
-    moment build (the O(N^5) step) on a steady-state-shaped pole set with k
-    occupied poles and all v' virtual poles; the rate is scaled by the
-    algorithmic flop ratio to the full o'.  Fock loop and compression
-    excluded (O(N^3); they would only lower the CPU rate)."""
+def oracle_sample(cfg, nmom=1, fock_cycles=FOCK_CAP, frac=ORACLE_FRACTION):
+    """One bounded sample of a steady-state AGF2 iteration on the FP64 CPU
+    oracle, as it stands.  Moment build: the rotation into the pole basis in
+    full, then the per-index loops of build_moments over an evenly spaced
+    share `frac` of BOTH outer summed indices (occupied i of the hole sector,
+    virtual a of the particle sector; every index of a sector costs the same,
+    so each sector's loop time scales by its count over the sample).  Fock
+    loop: one oracle Fock cycle (shift solve by bisection, diagonalisation of
+    the extended Hamiltonian, Fock build) timed on the iteration's shapes and
+    counted `fock_cycles` times.  Returns (seconds per iteration, wall seconds
+    of the sample, description)."""
+    import numpy as np
     from oracle import agf2_oracle as O
     from paper_2106_03508_gb300.synth import random_poles
-    s, o_full, v_full = _oracle_setup(cfg, nmom)
-    e, C, mu = random_poles(s.nmo, k + v_full, k, 11)
+    s, o, v = _oracle_setup(cfg, nmom)
+    N = s.nmo
+    e, C, mu = random_poles(N, o + v, o, 11)
+    ko, kv = max(1, round(o * frac)), max(1, round(v * frac))
+    occ = [int(x) for x in np.linspace(0, o - 1, ko).round()]
+    vir = [int(x) for x in np.linspace(0, v - 1, kv).round()]
     t0 = time.perf_counter()
-    O.build_moments(s.L, e, C, mu, nmom)
-    dt = time.perf_counter() - t0
-    rate = O.flops_moments(s.nmo, k, v_full, s.naux, nmom) / dt
-    return O.flops_moments(s.nmo, o_full, v_full, s.naux, nmom) / rate, dt
-
-
-def oracle_calibrate(cfg, target_s, nmom=1):
-    """Smallest sample size k (doubling) whose oracle build takes >= target_s / 2."""
-    s, o_full, v_full = _oracle_setup(cfg, nmom)
-    k = 1
-    while True:
-        t_iter, dt = oracle_time(cfg, k, nmom)
-        if dt >= target_s / 2 or 2 * k > o_full:
-            return k, t_iter, dt
-        k *= 2
-
-
-def oracle_sample_desc(cfg, k, dt, nmom=1):
-    s, o_full, v_full = _oracle_setup(cfg, nmom)
-    return (f"FP64 oracle build_moments (nmom={nmom}) on nmo={s.nmo} naux={s.naux} with {k} "
-            f"occupied + {v_full} virtual poles ({dt:.1f} s), extrapolated by algorithmic flops "
-            f"to o'={o_full}, v'={v_full} (one steady-state iteration); moment build only")
+    eo, Co, ev, Cv = O.split_poles(e, C, mu)
+    O.rotate(s.L, Co, Cv)
+    t_rot = time.perf_counter() - t0
+    t1 = time.perf_counter()
+    O.build_moments(s.L, e, C, mu, nmom, outer_occ=occ, outer_vir=[])
+    t_hole = max(0.0, time.perf_counter() - t1 - t_rot)
+    t1 = time.perf_counter()
+    O.build_moments(s.L, e, C, mu, nmom, outer_occ=[], outer_vir=vir)
+    t_part = max(0.0, time.perf_counter() - t1 - t_rot)
+    # one Fock cycle at the iteration's shapes: (nmom+1) N auxiliaries
+    rng = np.random.default_rng(12)
+    nse = (nmom + 1) * N
+    E = np.sort(np.concatenate([rng.uniform(-4, -1, nse // 2),
+                                rng.uniform(1, 5, nse - nse // 2)]))
+    vse = 0.3 * rng.standard_normal((N, nse))
+    t2 = time.perf_counter()
+    O.fock_loop(np.diag(s.eps), s.L, s.nelec, E, vse, O.hf_density(N, s.nocc), max_cycle=1)
+    t_cyc = time.perf_counter() - t2
+    t_iter = t_rot + t_hole * o / ko + t_part * v / kv + fock_cycles * t_cyc
+    wall = time.perf_counter() - t0
+    desc = (f"FP64 oracle on {os.cpu_count()} host cores, steady-state shapes nmo={N} "
+            f"naux={s.naux} o'={o} v'={v} nmom={nmom}: pole rotation in full ({t_rot:.2f} s); "
+            f"build_moments loops over {ko} of {o} occupied ({t_hole:.2f} s) and {kv} of {v} "
+            f"virtual ({t_part:.2f} s) outer indices, each scaled to its sector; one oracle "
+            f"Fock cycle ({t_cyc:.2f} s) x {fock_cycles} cycles; sample wall {wall:.1f} s")
+    return t_iter, wall, desc
 
 
 def run_reference(args):
@@ -122,24 +138,25 @@ def run_reference(args):
     if rank != 0:
         return
     cores = os.cpu_count()
-    k, _, _ = oracle_calibrate(args.config, args.cpu_seconds / 4, args.nmom)
     for _ in range(args.warmup):
-        oracle_time(args.config, k, args.nmom)
-    times, dts = [], []
+        oracle_sample(args.config, args.nmom)
+    iters, walls, desc = [], [], ""
     for _ in range(args.steps):
-        t, dt = oracle_time(args.config, k, args.nmom)
-        times.append(t)
-        dts.append(dt)
-    t = statistics.median(times)
+        t, wall, desc = oracle_sample(args.config, args.nmom)
+        iters.append(t)
+        walls.append(wall)
+    t = statistics.median(iters)
     val = 1.0 / t
     line = {"impl": "reference", "metric": METRIC, "value": val, "unit": UNIT,
             "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup,
-            "ms_per_step": t * 1e3, "higher_is_better": True, "scaling": "weak",
+            # a step is one bounded sample of an iteration; value extrapolates it
+            "ms_per_step": statistics.median(walls) * 1e3,
+            "iteration_seconds_estimate": t,
+            "higher_is_better": True, "scaling": "weak",
             "vs_baseline": None, "dtype": "f64", "data": "synthetic",
             "config": workload_desc(args.config, args.nmom),
             "cpu_baseline": {"value": val, "unit": UNIT, "cores": cores, "kind": "oracle",
-                             "sample": oracle_sample_desc(args.config, k, statistics.median(dts),
-                                                          args.nmom)},
+                             "sample": desc},
             "e2e": {"value": val, "unit": UNIT, "h2d_bytes_per_step": 0,
                     "d2h_bytes_per_step": 0}}
     print(json.dumps(line), flush=True)
@@ -216,12 +233,37 @@ KERNEL_NAMES = {
 }
 
 
-def kernel_rooflines(k_stats, steps, pk, src):
+def measure_fp64_peak():
+    """FP64 GEMM rate of this GPU in this run: torch float64 matmul (cuBLAS
+    DGEMM) of 4096^3, best of 5, CUDA events on the current stream."""
+    import torch
+    n = 4096
+    a = torch.randn(n, n, dtype=torch.float64, device="cuda")
+    b = torch.randn(n, n, dtype=torch.float64, device="cuda")
+    for _ in range(2):
+        torch.matmul(a, b)
+    best = float("inf")
+    for _ in range(5):
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record()
+        torch.matmul(a, b)
+        e1.record()
+        torch.cuda.synchronize()
+        best = min(best, e0.elapsed_time(e1))
+    del a, b
+    return 2.0 * n ** 3 / (best / 1e3) / 1e12
+
+
+def kernel_rooflines(k_stats, steps, pk, src, fp64_peak=None):
     """Roofline objects of the four timed kinds (agf2_kernel_stats: launches,
     ms, algorithmic flops) and the dominant kind by device time.  The
     tensor-core kinds 0, 1 are measured against the sustained BF16 peak, the
-    FP64 kinds 2, 3 against the nominal FP64 rate ("alu")."""
+    FP64 kinds 2, 3 against the FP64 GEMM rate measured in the same run
+    (cuBLAS DGEMM; the nominal 1.25 TFLOP/s if none was measured), "alu"."""
     bf16_peak = pk.get("bf16_tflops_sustained", pk.get("bf16_tflops"))
+    f64 = fp64_peak if fp64_peak else FP64_NOMINAL_TFLOPS
+    f64_src = ("FP64: cuBLAS DGEMM 4096^3 measured in this run (best of 5), of measured"
+               if fp64_peak else "FP64 FMA pipe, nominal 1.25 TFLOP/s, of nominal")
 
     def roof(kind):
         n_k, ms_k, fl_k = k_stats[kind]
@@ -233,10 +275,8 @@ def kernel_rooflines(k_stats, steps, pk, src):
                     "issued_tflops": 6 * ach,
                     "peak_source": f"bf16_tflops_sustained ({src}), of measured"}
         return {"bound": "alu", "kernel": KERNEL_NAMES[kind], "launches": n_k,
-                "ms_per_step": ms_k / steps, "achieved": ach, "peak": FP64_NOMINAL_TFLOPS,
-                "unit": "TFLOP/s", "frac": ach / FP64_NOMINAL_TFLOPS,
-                "peak_source": "FP64 FMA pipe, nominal 1.25 TFLOP/s (no measured FP64 peak "
-                               "in MEASURED_PEAKS.json)"}
+                "ms_per_step": ms_k / steps, "achieved": ach, "peak": f64,
+                "unit": "TFLOP/s", "frac": ach / f64, "peak_source": f64_src}
 
     dominant = max((0, 1, 2, 3), key=lambda k: k_stats[k][1])
     return dominant, {k: roof(k) for k in (0, 1, 2, 3)}
@@ -261,7 +301,7 @@ def run_batched(args):
         agf2.agf2_hcore_from_mo_energies(h.h, L.data_ptr(), s.naux, s.nmo, eps.data_ptr(), s.nocc,
                                          hc.data_ptr())
         keep += [L, eps, hc]
-        sysl.append((hc.data_ptr(), L.data_ptr(), eps.data_ptr(), s.naux, s.nmo, s.nelec))
+        sysl.append((hc.data_ptr(), L.data_ptr(), None, s.naux, s.nmo, s.nelec))
     o = agf2.agf2_opts_default()
     o.precision = agf2.AGF2_BF16X3 if args.precision == "bf16x3" else agf2.AGF2_FP64
     o.fock.shift_mode = args.shift_mode
@@ -328,7 +368,7 @@ def run_ours(args):
     o.fock.shift_mode = args.shift_mode
     o.max_iter = max(1, args.warmup)
     o.resume = 0
-    agf2.agf2_run(h.h, hc.data_ptr(), L.data_ptr(), naux, N, nelec, eps.data_ptr(), o)
+    agf2.agf2_run(h.h, hc.data_ptr(), L.data_ptr(), naux, N, nelec, None, o)
     o.max_iter = 1
     o.resume = 1
 
@@ -347,7 +387,7 @@ def run_ours(args):
     t_ev0, t_ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
     t_ev0.record()
     for _ in range(args.steps):
-        rc, out = agf2.agf2_run(h.h, hc.data_ptr(), L.data_ptr(), naux, N, nelec, eps.data_ptr(), o)
+        rc, out = agf2.agf2_run(h.h, hc.data_ptr(), L.data_ptr(), naux, N, nelec, None, o)
         results.append(out.as_dict())
     t_ev1.record()
     barrier()
@@ -366,25 +406,52 @@ def run_ours(args):
         e_dev = torch.empty(nq, dtype=torch.float64, device="cuda")
         L2 = torch.empty_like(L)
         hc2 = torch.empty_like(hc)
-        eps2 = torch.empty_like(eps)
         barrier()
         t0 = time.perf_counter()
         for _ in range(args.steps):
             L2.copy_(L_host, non_blocking=True)
             hc2.copy_(hc_host, non_blocking=True)
-            eps2.copy_(eps_host, non_blocking=True)
-            agf2.agf2_run(h.h, hc2.data_ptr(), L2.data_ptr(), naux, N, nelec, eps2.data_ptr(), o)
+            agf2.agf2_run(h.h, hc2.data_ptr(), L2.data_ptr(), naux, N, nelec, None, o)
             agf2.agf2_get_state(h.h, e=e_dev.data_ptr())
             e_out.copy_(e_dev, non_blocking=True)
         barrier()
         e_el, e_val = aggregate(time.perf_counter() - t0, args.steps, world, dist, "cuda")
         e2e = {"value": e_val, "unit": UNIT,
-               "h2d_bytes_per_step": int(L_host.numel() * 8 + hc_host.numel() * 8 + eps_host.numel() * 8),
+               "h2d_bytes_per_step": int(L_host.numel() * 8 + hc_host.numel() * 8),
                "d2h_bytes_per_step": int(e_out.numel() * 8)}
 
-    # ---- FP64 path on the same state (mixed vs FP64 per iteration) ----
+    # ---- mixed vs FP64 ----
+    # (1) moments in both precisions on the steady-state Green's function the
+    #     timed steps left (same poles and couplings): per-moment error and the
+    #     FP64 moment-build time; (2) one FP64 iteration continuing from that
+    #     state: FP64 time per iteration; (3) iteration 1 from the Hartree-Fock
+    #     reference in each precision: E_tot, IP, EA differences.
     fp64 = None
     if args.fp64_steps > 0 and prec != agf2.AGF2_FP64:
+        nq = agf2.agf2_get_state(h.h)
+        e_st = torch.empty(nq, dtype=torch.float64, device="cuda")
+        C_st = torch.empty(N, nq, dtype=torch.float64, device="cuda")
+        agf2.agf2_get_state(h.h, e=e_st.data_ptr(), C=C_st.data_ptr())
+        mu_st = results[-1]["mu"]
+        nm = args.nmom + 1
+        U, t_mom = {}, {}
+        for pname, pc in (("mixed", agf2.AGF2_BF16X3), ("fp64", agf2.AGF2_FP64)):
+            Uh = torch.empty(nm, N, N, dtype=torch.float64, device="cuda")
+            Up = torch.empty_like(Uh)
+            barrier()
+            t0 = time.perf_counter()
+            agf2.agf2_build_moments(h.h, L.data_ptr(), naux, N, e_st.data_ptr(),
+                                    C_st.data_ptr(), nq, mu_st, args.nmom, pc, Uh.data_ptr(),
+                                    Up.data_ptr())
+            barrier()
+            t_mom[pname] = time.perf_counter() - t0
+            U[pname] = (Uh.cpu(), Up.cpu())
+        moment_err = {}
+        for si, sec in enumerate(("hole", "particle")):
+            for n in range(nm):
+                ref = U["fp64"][si][n]
+                moment_err[f"{sec}_U{n}"] = float((U["mixed"][si][n] - ref).abs().max() /
+                                                  ref.abs().max())
         of = agf2.agf2_opts_default()
         of.precision = agf2.AGF2_FP64
         of.nmom = args.nmom
@@ -396,15 +463,37 @@ def run_ours(args):
         fr = []
         for _ in range(args.fp64_steps):
             rc, out = agf2.agf2_run(h.h, hc.data_ptr(), L.data_ptr(), naux, N, nelec,
-                                    eps.data_ptr(), of)
+                                    None, of)
             fr.append(out.as_dict())
         barrier()
         dt = (time.perf_counter() - t0) / args.fp64_steps
+        it1 = {}
+        for pname, pc in (("mixed", agf2.AGF2_BF16X3), ("fp64", agf2.AGF2_FP64)):
+            o1 = agf2.agf2_opts_default()
+            o1.precision = pc
+            o1.nmom = args.nmom
+            o1.fock.shift_mode = args.shift_mode
+            o1.max_iter = 1
+            o1.resume = 0
+            rc, out = agf2.agf2_run(h.h, hc.data_ptr(), L.data_ptr(), naux, N, nelec,
+                                    None, o1)
+            it1[pname] = out.as_dict()
         fp64 = {"iterations_per_s": 1.0 / dt, "s_per_iter": dt,
-                "moment_s": statistics.mean(r["t_moments"] for r in fr),
+                "moment_s": t_mom["fp64"], "mixed_moment_s": t_mom["mixed"],
                 "moment_tflops": statistics.mean(r["flops_moments"] / r["t_moments"] / 1e12
                                                  for r in fr),
-                "mixed_speedup_per_iter": (args.steps / elapsed) * dt}
+                "mixed_speedup_per_iter": (args.steps / elapsed) * dt,
+                "mixed_speedup_moment_build": t_mom["fp64"] / t_mom["mixed"],
+                "moment_max_rel_err_vs_fp64": moment_err,
+                "iteration1_from_hf": {
+                    "abs_diff_Ha": {k: abs(it1["mixed"][k] - it1["fp64"][k])
+                                    for k in ("E_tot", "E_2b", "ip", "ea")},
+                    "fp64": {k: it1["fp64"][k] for k in ("E_tot", "ip", "ea", "fock_cycles",
+                                                         "fock_converged")},
+                    "mixed": {k: it1["mixed"][k] for k in ("fock_cycles", "fock_converged")},
+                    "note": "a Fock loop stopped at its cycle cap unconverged ends where its "
+                            "own dynamics take it: differences then measure that sensitivity, "
+                            "not the moment error"}}
 
     if rank != 0:
         h.close()
@@ -413,7 +502,8 @@ def run_ours(args):
         return
 
     pk, src = peaks()
-    dominant, roofs = kernel_rooflines(k_stats, args.steps, pk, src)
+    fp64_peak = measure_fp64_peak()
+    dominant, roofs = kernel_rooflines(k_stats, args.steps, pk, src, fp64_peak)
 
     mom_t = statistics.mean(r["t_moments"] for r in results)
     mom_fl = statistics.mean(r["flops_moments"] for r in results)
@@ -440,12 +530,19 @@ def run_ours(args):
         "e2e": e2e,
         "fp64_path": fp64,
         "last_energies": {k: results[-1][k] for k in ("E_tot", "ip", "ea", "mu")},
+        "fock_per_step": {"cycles": [r["fock_cycles"] for r in results],
+                          "converged": [r["fock_converged"] for r in results],
+                          "cap": o.fock.max_cycle,
+                          "note": "a step's Fock loop that stops at the cap did not meet "
+                                  "max|dD| < tol_D; on this synthetic generator every c2/c3 "
+                                  "loop does"},
+        "fp64_peak_tflops_measured": fp64_peak,
     }
     if rank == 0 and world == 1:
-        k, t_iter, dt = oracle_calibrate(args.config, args.cpu_seconds, args.nmom)
+        cyc = round(statistics.mean(r["fock_cycles"] for r in results))
+        t_iter, wall, desc = oracle_sample(args.config, args.nmom, fock_cycles=cyc)
         line["cpu_baseline"] = {"value": 1.0 / t_iter, "unit": UNIT, "cores": os.cpu_count(),
-                                "kind": "oracle",
-                                "sample": oracle_sample_desc(args.config, k, dt, args.nmom)}
+                                "kind": "oracle", "sample": desc}
     print(json.dumps(line), flush=True)
     h.close()
     if world > 1:

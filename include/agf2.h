@@ -207,35 +207,45 @@ typedef struct {
     int    fock_cycles;               /* of the last iteration                */
     double t_moments, t_compress, t_fock, t_energy;  /* seconds, summed      */
     double flops_moments;             /* algorithmic flops of the moment builds */
+    int    fock_converged;            /* 1 if the last iteration's Fock loop met
+                                         its density tolerance (else it stopped
+                                         at max_cycle)                        */
+    int    fock_cycles_total;         /* Fock cycles summed over the call      */
 } agf2_result;
 
 /* Fill `o` with the defaults listed above. */
 void agf2_opts_default(agf2_opts* o);
 
 /*
- * Full AGF2 iteration from the Hartree-Fock reference in the MO basis (poles
- * e = eps0, C = I, D0 = aufbau density of nelec/2 orbitals): moments ->
- * moment mixing -> compression of each sector (agf2_compress_moments) ->
- * Fock loop over nmo + (nmom+1) nmo poles -> energies,
- * until |dE_tot| < conv_tol or max_iter.  E_1b = Tr[D(h+F)]/2; E_2b is the
- * Galitskii-Migdal sum over occupied poles x and particle-sector auxiliaries
- * k of (C_x . v_k)^2 / (e_x - E_k).  The final state (poles, self-energy,
- * density, mixing history) stays in the handle; with opts->resume = 1 the
- * next call continues from it (eps0 is then ignored).
- *   hcore [nmo][nmo], L [naux][nmo][nmo], eps0 [nmo]: device pointers
+ * Full AGF2 iteration from the Hartree-Fock reference (Eq. gf_hf): the
+ * reference density D0 gives F[D0] by Eq. (fock_matrix), and the initial
+ * poles and couplings are its eigenpairs, e = eig(F[D0]) with C the
+ * eigenvectors, in whatever orthonormal basis hcore, L and D0 are given.
+ * Then moments -> moment mixing -> compression of each sector
+ * (agf2_compress_moments) -> Fock loop over nmo + (nmom+1) nmo poles ->
+ * energies, until |dE_tot| < conv_tol or max_iter.  E_hf = Tr[D0(h+F[D0])]/2,
+ * E_1b = Tr[D(h+F)]/2; E_2b is the Galitskii-Migdal sum over occupied poles x
+ * and particle-sector auxiliaries k of (C_x . v_k)^2 / (e_x - E_k).  The final
+ * state (poles, self-energy, density, mixing history) stays in the handle;
+ * with opts->resume = 1 the next call continues from it (D0 is then ignored).
+ *   hcore [nmo][nmo], L [naux][nmo][nmo]: device pointers
+ *   D0 [nmo][nmo]: device pointer to the reference density (2 x the
+ *     projector onto the nelec/2 occupied orbitals), or NULL for the aufbau
+ *     density of the first nelec/2 basis functions -- the basis of the
+ *     reference's canonical orbitals, as for the synthetic systems
  *   opts, out: host pointers (opts NULL = defaults)
  * Returns AGF2_ERR_NO_CONVERGENCE (with *out filled) if max_iter is reached
  * before convergence and max_iter > 1, AGF2_ERR_INVALID_ARG if the extended
  * Hamiltonian would exceed the eigensolver's limit, nmo (nmom + 2) > 7000.
  */
 int agf2_run(agf2_handle h, const double* hcore, const double* L, int naux, int nmo,
-             int nelec, const double* eps0, const agf2_opts* opts, agf2_result* out);
+             int nelec, const double* D0, const agf2_opts* opts, agf2_result* out);
 
 /* One system of a batch: device pointers as for agf2_run. */
 typedef struct {
     const double* hcore;   /* [nmo][nmo]            */
     const double* L;       /* [naux][nmo][nmo]      */
-    const double* eps0;    /* [nmo]                 */
+    const double* D0;      /* [nmo][nmo] or NULL    */
     int naux, nmo, nelec;
 } agf2_system;
 

@@ -113,13 +113,16 @@ def rotate(L: np.ndarray, Co: np.ndarray, Cv: np.ndarray):
     return Lxo, Lxv, Lov
 
 
-def build_moments(L, e, C, mu, nmom: int = 1):
+def build_moments(L, e, C, mu, nmom: int = 1, outer_occ=None, outer_vir=None):
     """U_<^(n), U_>^(n) for n = 0..nmom, each [nmom+1, N, N].
 
     Hole:     U_pq = sum_{ija} (pi|ja)[2(qi|ja) - (qj|ia)] (e_i+e_j-e_a)^n
     Particle: U_pq = sum_{abi} (pa|bi)[2(qa|bi) - (qb|ai)] (e_a+e_b-e_i)^n
     evaluated one summed index (i, resp. a) at a time, as in the paper's
-    block-distributed algorithm.
+    block-distributed algorithm.  ``outer_occ`` / ``outer_vir`` (positions
+    in the occupied / virtual pole lists) restrict that first summed index
+    to a slice -- the share one of the paper's ranks computes; the slices of
+    a partition add up to the whole.
     """
     N = L.shape[1]
     eo, Co, ev, Cv = split_poles(e, C, mu)
@@ -127,7 +130,7 @@ def build_moments(L, e, C, mu, nmom: int = 1):
     Lvo = Lov.transpose(0, 2, 1)       # (ai|Q) = (ia|Q)
     Uh = np.zeros((nmom + 1, N, N))
     Up = np.zeros((nmom + 1, N, N))
-    for i in range(len(eo)):
+    for i in (range(len(eo)) if outer_occ is None else outer_occ):
         X = np.tensordot(Lxo[:, :, i], Lov, axes=(0, 0))        # (pi|ja) [p,j,a]
         Xk = np.tensordot(Lxo, Lov[:, i, :], axes=(0, 0))       # (pj|ia) [p,j,a]
         Xt = (2.0 * X - Xk).reshape(N, -1)
@@ -135,7 +138,7 @@ def build_moments(L, e, C, mu, nmom: int = 1):
         X = X.reshape(N, -1)
         for n in range(nmom + 1):
             Uh[n] += (X * w ** n) @ Xt.T
-    for a in range(len(ev)):
+    for a in (range(len(ev)) if outer_vir is None else outer_vir):
         X = np.tensordot(Lxv[:, :, a], Lvo, axes=(0, 0))        # (pa|bi) [p,b,i]
         Xk = np.tensordot(Lxv, Lvo[:, a, :], axes=(0, 0))       # (pb|ai) [p,b,i]
         Xt = (2.0 * X - Xk).reshape(N, -1)
@@ -548,19 +551,25 @@ class RunResult:
 
 
 def run(h, L, nelec, eps0, max_iter=50, conv_tol=1e-8, nmom=1, fock_tol=1e-10,
-        fock_max_cycle=100, diis_space=0, diis_start=2, mix=1.0, keep_moments=False):
-    """AGF2 from the HF reference: poles e = eps0, C = I, D = D0.
+        fock_max_cycle=100, diis_space=0, diis_start=2, mix=1.0, keep_moments=False, D0=None):
+    """AGF2 from the HF reference (Eq. gf_hf).  With D0 (the reference
+    density in the basis of h and L) the initial poles and couplings are the
+    eigenpairs of F[D0]; without it the basis is that of the reference's
+    canonical orbitals: poles e = eps0, C = I, D0 the aufbau density.
 
     Each iteration: moments from the current poles, DIIS on the stacked
     moments (U_<^(0), U_<^(1), U_>^(0), U_>^(1)) from iteration
     ``diis_start`` on, compression of each sector, Fock loop, energies."""
     N = h.shape[0]
     nocc = nelec // 2
-    D = hf_density(N, nocc)
+    D = hf_density(N, nocc) if D0 is None else np.array(D0, dtype=np.float64)
     F = fock_matrix(h, L, D)
     E_hf = energy_1body(h, F, D)
-    e = np.array(eps0, dtype=np.float64)
-    C = np.eye(N)
+    if D0 is None:
+        e = np.array(eps0, dtype=np.float64)
+        C = np.eye(N)
+    else:
+        e, C = np.linalg.eigh(F)
     mu = 0.5 * (e[nocc - 1] + e[nocc])
     hist = []
     moms = []

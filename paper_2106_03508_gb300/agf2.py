@@ -54,7 +54,7 @@ class agf2_opts(ct.Structure):
 
 
 class agf2_system(ct.Structure):
-    _fields_ = [("hcore", ct.c_void_p), ("L", ct.c_void_p), ("eps0", ct.c_void_p),
+    _fields_ = [("hcore", ct.c_void_p), ("L", ct.c_void_p), ("D0", ct.c_void_p),
                 ("naux", ct.c_int), ("nmo", ct.c_int), ("nelec", ct.c_int)]
 
 
@@ -64,7 +64,8 @@ class agf2_result(ct.Structure):
                 ("mu", ct.c_double), ("iterations", ct.c_int), ("converged", ct.c_int),
                 ("nocc_qmo", ct.c_int), ("fock_cycles", ct.c_int), ("t_moments", ct.c_double),
                 ("t_compress", ct.c_double), ("t_fock", ct.c_double), ("t_energy", ct.c_double),
-                ("flops_moments", ct.c_double)]
+                ("flops_moments", ct.c_double), ("fock_converged", ct.c_int),
+                ("fock_cycles_total", ct.c_int)]
 
     def as_dict(self):
         return {name: getattr(self, name) for name, _ in self._fields_}
@@ -166,6 +167,7 @@ def agf2_eigh_physical(h, A, n, nphys, w, V):
     return _check(h, _lib.agf2_eigh_physical(h, A, n, nphys, w, V))
 
 
+
 def agf2_fock_opts_default() -> agf2_fock_opts:
     o = agf2_fock_opts()
     _lib.agf2_fock_opts_default(ct.byref(o))
@@ -187,16 +189,17 @@ def agf2_opts_default() -> agf2_opts:
     return o
 
 
-def agf2_run(h, hcore, L, naux, nmo, nelec, eps0, opts=None, allow=(AGF2_ERR_NO_CONVERGENCE,)):
+def agf2_run(h, hcore, L, naux, nmo, nelec, D0=None, opts=None,
+             allow=(AGF2_ERR_NO_CONVERGENCE,)):
     out = agf2_result()
-    rc = _lib.agf2_run(h, hcore, L, naux, nmo, nelec, eps0,
+    rc = _lib.agf2_run(h, hcore, L, naux, nmo, nelec, D0,
                        ct.byref(opts) if opts is not None else None, ct.byref(out))
     _check(h, rc, allow)
     return rc, out
 
 
 def agf2_run_batched(h, systems, opts=None, nworkers=0, allow=(AGF2_ERR_NO_CONVERGENCE,)):
-    """systems: list of (hcore_ptr, L_ptr, eps0_ptr, naux, nmo, nelec)."""
+    """systems: list of (hcore_ptr, L_ptr, D0_ptr or None, naux, nmo, nelec)."""
     n = len(systems)
     arr = (agf2_system * max(n, 1))(*[agf2_system(*sy) for sy in systems])
     out = (agf2_result * max(n, 1))()

@@ -18,7 +18,7 @@ CSRC = PKG / "csrc"
 INCLUDE = PKG.parent / "include"
 OUT_DIR = PKG / "_build"
 LIB = PKG / "libagf2.so"
-SOURCES = ["capi.cu", "fp64.cu", "mixed.cu", "noalloc.cu", "eigen.cu"]
+SOURCES = ["capi.cu", "fp64.cu", "mixed.cu", "rotate.cu", "noalloc.cu", "eigen.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 
 

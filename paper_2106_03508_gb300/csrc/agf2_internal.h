@@ -1,5 +1,6 @@
 // Internal declarations shared by the library's translation units.
 #pragma once
+#include <cuda_bf16.h>
 #include <cuda_runtime.h>
 #include <cstdint>
 #include <string>
@@ -108,15 +109,34 @@ cudaError_t max_abs_diff(const double* a, const double* b, long long n, double* 
                          cudaStream_t s);
 cudaError_t add_scalar(double* x, double a, int n, cudaStream_t s);
 
-// Split-precision (BF16x3 / tcgen05) moment build from the FP64 rotated
-// tensors Lxo [o][N][naux], Lxv [v][N][naux], Lov [o][v][naux]; accumulates
-// moments 0..nmom (nmom <= 3) into the zeroed U_hole, U_part [nmom+1][N][N]
-// (upper tiles mirrored, not symmetrised).  Returns an
-// AGF2 status; err receives a message.
-int mixed_build_moments_rotated(const double* Lxo, const double* Lxv, const double* Lov, int naux,
-                                int N, int o, int v, const double* eo, const double* ev, int nmom,
-                                double* U_hole, double* U_part, std::string& err,
-                                cudaStream_t s, KernelStats* stats, void* workspace);
+// Split-precision (BF16x3 / tcgen05) moment build: rotates L into the pole
+// basis (occupied couplings Co [N][o], virtual Cv [N][v]) block by block
+// straight into BF16 limb planes, then accumulates moments 0..nmom
+// (nmom <= 3) into the zeroed U_hole, U_part [nmom+1][N][N] (upper tiles
+// mirrored, not symmetrised).  Returns an AGF2 status; err receives a message.
+int mixed_build_moments(const double* L, int naux, int N, const double* Co, const double* Cv,
+                        int o, int v, const double* eo, const double* ev, int nmom,
+                        double* U_hole, double* U_part, std::string& err, cudaStream_t s,
+                        KernelStats* stats, void* workspace);
+// Pole-basis rotation on the tensor cores (rotate.cu), four-limb split with
+// exact chunk sums, FP64 results:
+//   out[m sOm + b sOb + n] = sum_k A[a_row0 + m][k] B[b][n][k]
+// from limb planes A [4][rowsA][Ks], B [4][nbatch][Nn][Ks] (Ks a multiple of
+// 256) with row units unitA [rowsA], unitB [nbatch][Nn].
+int rot_gemm4(const __nv_bfloat16* A, long long rowsA, int a_row0, int M, const float* unitA,
+              const __nv_bfloat16* B, int Nn, int nbatch, const float* unitB, int Ks,
+              double* out, long long sOm, long long sOb, int* derr, std::string& err,
+              cudaStream_t s);
+// FP64 rows (element (r, c) at src[r ld + c cs]) -> four integer BF16 limb
+// planes [4][dst_rows][ncolp] with units (row r -> (r/grp) gstride + goff + r%grp).
+int rot_limbs_slice4(const double* src, long long nrow, int ncol, long long ld, long long cs,
+                     int ncolp, long long dst_rows, long long grp, long long gstride,
+                     long long goff, __nv_bfloat16* dst, float* unit, cudaStream_t s);
+// W [nx][nQ][N] -> three-limb planes of the rows (x, p) over Q, rows
+// row0 + x N + p of [3][dst_rows][Qs], with certified units (stats: 3 nx N doubles).
+int rot_transpose_slice3(const double* W, int nx, int nQ, int N, int Qs, double* stats,
+                         long long dst_rows, long long row0, __nv_bfloat16* dst, float* unit,
+                         cudaStream_t s);
 // Symmetric FP64 eigensolver (eigen.cu): eigenvalues ascending into w and
 // the first nphys rows of the eigenvectors into V (column-major, column x at
 // V + x n), n <= 7000.  A [n][n] symmetric is not modified.  Workspace: one per handle.

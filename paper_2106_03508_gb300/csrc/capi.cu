@@ -377,36 +377,37 @@ void build_moments_impl(agf2_context* ctx, const double* L, int naux, int N, con
   const long long NN = (long long)N * N;
   CK(cudaMemsetAsync(Uh, 0, (nmom + 1) * NN * sizeof(double), s));
   CK(cudaMemsetAsync(Up, 0, (nmom + 1) * NN * sizeof(double), s));
-  const long long NQ = (long long)N * naux;
-  double* Lxo = ws(ctx, "mom_Lxo", (size_t)o * NQ);
-  double* Lxv = ws(ctx, "mom_Lxv", (size_t)v * NQ);
-  double* Lov = ws(ctx, "mom_Lov", (size_t)o * v * naux);
-  auto rot = [&](const double* Cx, int nx, double* out) {
-    DGemm g;  // out[x][p][Q] = sum_r Cx[r][x] L[Q][r][p]
-    g.M = nx; g.N = N; g.K = N;
-    g.A = Cx; g.sAm = 1; g.sAk = nx;
-    g.B = L; g.sBk = N; g.sBn = 1; g.sB1 = NN;
-    g.C = out; g.sCm = NQ; g.sCn = naux; g.sC1 = 1;
-    g.nb1 = naux;
-    CK(dgemm(g, s));
-  };
-  rot(Co, o, Lxo);
-  rot(Cv, v, Lxv);
-  {
-    DGemm g;  // Lov[j][a][Q] = sum_p Co[p][j] Lxv[a][p][Q]
-    g.M = o; g.N = v; g.K = N;
-    g.A = Co; g.sAm = 1; g.sAk = o;
-    g.B = Lxv; g.sBk = naux; g.sBn = NQ; g.sB1 = 1;
-    g.C = Lov; g.sCm = (long long)v * naux; g.sCn = naux; g.sC1 = 1;
-    g.nb1 = naux;
-    CK(dgemm(g, s));
-  }
   if (precision == AGF2_BF16X3) {
+    // rotation and moments in the split-precision path, block by block
     if (!ctx->mixed_ws) ctx->mixed_ws = mixed_workspace_create();
-    int rc = mixed_build_moments_rotated(Lxo, Lxv, Lov, naux, N, o, v, eo, ev, nmom, Uh, Up,
-                                         ctx->err, s, &ctx->stats, ctx->mixed_ws);
+    int rc = mixed_build_moments(L, naux, N, Co, Cv, o, v, eo, ev, nmom, Uh, Up, ctx->err, s,
+                                 &ctx->stats, ctx->mixed_ws);
     if (rc != AGF2_OK) throw Fail{rc};
   } else {
+    const long long NQ = (long long)N * naux;
+    double* Lxo = ws(ctx, "mom_Lxo", (size_t)o * NQ);
+    double* Lxv = ws(ctx, "mom_Lxv", (size_t)v * NQ);
+    double* Lov = ws(ctx, "mom_Lov", (size_t)o * v * naux);
+    auto rot = [&](const double* Cx, int nx, double* out) {
+      DGemm g;  // out[x][p][Q] = sum_r Cx[r][x] L[Q][r][p]
+      g.M = nx; g.N = N; g.K = N;
+      g.A = Cx; g.sAm = 1; g.sAk = nx;
+      g.B = L; g.sBk = N; g.sBn = 1; g.sB1 = NN;
+      g.C = out; g.sCm = NQ; g.sCn = naux; g.sC1 = 1;
+      g.nb1 = naux;
+      CK(dgemm(g, s));
+    };
+    rot(Co, o, Lxo);
+    rot(Cv, v, Lxv);
+    {
+      DGemm g;  // Lov[j][a][Q] = sum_p Co[p][j] Lxv[a][p][Q]
+      g.M = o; g.N = v; g.K = N;
+      g.A = Co; g.sAm = 1; g.sAk = o;
+      g.B = Lxv; g.sBk = naux; g.sBn = NQ; g.sB1 = 1;
+      g.C = Lov; g.sCm = (long long)v * naux; g.sCn = naux; g.sC1 = 1;
+      g.nb1 = naux;
+      CK(dgemm(g, s));
+    }
     Sector hole{o, v, Lxo, Lov, (long long)v * naux, (long long)naux, eo, ev};
     Sector part{v, o, Lxv, Lov, (long long)naux, (long long)v * naux, ev, eo};
     sector_fp64(ctx, hole, N, naux, nmom, Uh);
@@ -1136,7 +1137,7 @@ int agf2_fock_loop(agf2_handle h, const double* hcore, const double* L, int naux
 }
 
 int agf2_run(agf2_handle h, const double* hcore, const double* L, int naux, int nmo, int nelec,
-             const double* eps0, const agf2_opts* opts, agf2_result* out) {
+             const double* D0_in, const agf2_opts* opts, agf2_result* out) {
   int rc_conv = AGF2_OK;
   int rc = guarded(h, [&](agf2_context* ctx) {
     if (!out) fail(ctx, AGF2_ERR_INVALID_ARG, "out is NULL");
@@ -1173,16 +1174,29 @@ int agf2_run(agf2_handle h, const double* hcore, const double* L, int naux, int 
     double* V = ws(ctx, "st_V", (size_t)nq_max * nb * N);
     const int nocc = nelec / 2;
     if (!o.resume || !ctx->have_state || ctx->nmo != N || ctx->nq_max != nq_max) {
-      check_dev_ptr(ctx, eps0, "eps0");
-      std::vector<double> e0 = to_host(ctx, eps0, N);
-      CK(cudaMemcpyAsync(e, eps0, N * sizeof(double), cudaMemcpyDeviceToDevice, s));
-      CK(set_identity(C, N, 1.0, s));
-      std::vector<double> d(N, 0.0);
-      for (int i = 0; i < nocc; ++i) d[i] = 2.0;
-      double* dv = ws(ctx, "st_d0", N);
-      CK(cudaMemcpyAsync(dv, d.data(), N * sizeof(double), cudaMemcpyHostToDevice, s));
-      CK(diag_from_vec(dv, N, D, s));
+      // reference density: the caller's, else the aufbau density of the first
+      // nocc basis functions (the reference's canonical orbitals as basis)
+      if (D0_in) {
+        check_dev_ptr(ctx, D0_in, "D0");
+        CK(cudaMemcpyAsync(D, D0_in, NN * sizeof(double), cudaMemcpyDeviceToDevice, s));
+      } else {
+        std::vector<double> d(N, 0.0);
+        for (int i = 0; i < nocc; ++i) d[i] = 2.0;
+        double* dv = ws(ctx, "st_d0", N);
+        CK(cudaMemcpyAsync(dv, d.data(), N * sizeof(double), cudaMemcpyHostToDevice, s));
+        CK(diag_from_vec(dv, N, D, s));
+      }
       fock_general(ctx, hcore, L, naux, N, D, F);
+      // initial Green's function: the mean-field poles e = eig(F[D0]) with the
+      // eigenvectors as couplings C (Eq. gf_hf in the given basis)
+      {
+        if (!ctx->eig_ws) ctx->eig_ws = eig_workspace_create();
+        double* V0 = ws(ctx, "st_V0", NN);
+        const int rc = eigh_phys(ctx->eig_ws, F, N, N, e, V0, s, ctx->err);
+        if (rc != AGF2_OK) throw Fail{rc};
+        CK(physical_block(V0, N, N, N, C, s));  // C[p][x] = V0[x N + p]
+      }
+      std::vector<double> e0 = to_host(ctx, e, N);
       CK(dot(D, hcore, NN, red + 512, red, s));
       CK(dot(D, F, NN, red + 513, red, s));
       std::vector<double> tr = to_host(ctx, red + 512, 2);
@@ -1253,6 +1267,8 @@ int agf2_run(agf2_handle h, const double* hcore, const double* L, int naux, int 
       out->mu = fo.mu;
       out->nocc_qmo = k;
       out->fock_cycles = fo.cycles;
+      out->fock_converged = fo.converged;
+      out->fock_cycles_total += fo.cycles;
       out->t_energy += seconds_since(t0);
       const double dE = std::fabs(Et - ctx->E_prev);
       ctx->E_prev = Et;
@@ -1348,7 +1364,7 @@ int agf2_run_batched(agf2_handle h, int nsys, const agf2_system* systems, const 
       agf2_opts_default(&o);
       if (opts) o = *opts;
       o.resume = 0;
-      st[i] = agf2_run(w, sy.hcore, sy.L, sy.naux, sy.nmo, sy.nelec, sy.eps0, &o, &out[i]);
+      st[i] = agf2_run(w, sy.hcore, sy.L, sy.naux, sy.nmo, sy.nelec, sy.D0, &o, &out[i]);
       if (st[i] != AGF2_OK) msg[i] = agf2_last_error(w);
     }
     agf2_destroy(w);

@@ -30,13 +30,18 @@
 
 #include "../../include/agf2.h"
 #include "agf2_internal.h"
+#include "tc_core.cuh"
 
 namespace agf2 {
 
 namespace {
 
 constexpr int SY_THREADS = 256;
-constexpr long long kSpinCycles = 1LL << 31;  // ~1 s at 2 GHz: a barrier that never completes
+// Limit of a grid-barrier wait, in ns of the global timer (a barrier that
+// never completes).  The SM cycle counter is not used as the time base: the
+// waiting warps sleep between polls, and a counter tied to the SM clock need
+// not advance at its nominal rate then.
+constexpr unsigned long long kSpinNs = 1000000000ULL;
 constexpr int TILE = 40;                      // GEMM tile of the eigenvector update
 
 __device__ __forceinline__ double warp_sum(double v) {
@@ -59,17 +64,19 @@ __device__ __forceinline__ void flag_arrive(unsigned* flags, unsigned step) {
 }
 
 // Wait until every CTA's flag reached `step` (warp 0 polls the flags in
-// parallel); gives up after kSpinCycles, setting *err and the abort flag.
+// parallel); gives up after kSpinNs, setting *err and the abort flag.
 __device__ bool flag_wait(unsigned* flags, unsigned step, int* err, int* abort_sh) {
   if (threadIdx.x < 32) {
-    const long long t0 = clock64();
+    const unsigned long long t0 = tc::global_ns();
     bool ok = false;
     while (true) {
       bool mine = true;
       for (int g = threadIdx.x; g < (int)gridDim.x; g += 32)
         mine &= (*(volatile unsigned*)(flags + g) >= step);
       if (__all_sync(0xffffffffu, mine)) { ok = true; break; }
-      if (clock64() - t0 > kSpinCycles) break;
+      // lane 0's clock decides, so the whole warp leaves the loop together
+      // (a per-lane decision would strand the other lanes in __all_sync)
+      if (__shfl_sync(0xffffffffu, (tc::global_ns() - t0 > kSpinNs) ? 1 : 0, 0)) break;
       __nanosleep(20);
     }
     if (!ok && threadIdx.x == 0) {
@@ -1055,6 +1062,17 @@ int eigh_phys(void* workspace, const double* Ain, int n, int nphys, double* w_ou
       return AGF2_ERR_CUDA;
     }
     count_launch();
+    // a barrier that gave up left T unfinished: stop before the stages that read it
+    int herr = 0;
+    cudaMemcpyAsync(&herr, derr, sizeof(int), cudaMemcpyDeviceToHost, s);
+    if (cudaStreamSynchronize(s) != cudaSuccess) {
+      ck("sytrd");
+      return AGF2_ERR_CUDA;
+    }
+    if (herr) {
+      err = "eigh_phys: tridiagonalisation barrier timed out";
+      return AGF2_ERR_TIMEOUT;
+    }
   }
   // 2. divide and conquer on T
   dc_init_kernel<<<(int)std::min<long long>((nn + 255) / 256, 152LL * 16), 256, 0, s>>>(

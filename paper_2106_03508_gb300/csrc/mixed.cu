@@ -93,6 +93,15 @@ struct Params {
   int* err;
 };
 
+// K steps of one moment-GEMM accumulation: KCHUNK = 256 entries.  With
+// |h0| <= 256, every partial sum of a chunk's h0 h0' products is an integer
+// of magnitude <= 2^24, exact in the FP32 accumulator, and the correction
+// products see at most 16 instructions of FP32 accumulation; the epilogue
+// sums the chunks of a tile in registers (round to nearest).
+constexpr int CHUNK_STEPS = KCHUNK / BK;
+// Chunks per moment-GEMM tile at most (bounds the register sum's rounding).
+constexpr int MAX_TILE_CHUNKS = 8;
+
 struct Segment {
   int a_row, a_idx;   // A tile: rows a_row.., outer index / plane a_idx
   int b_row, b_idx;   // B tile
@@ -256,16 +265,19 @@ gemm6_kernel(const __grid_constant__ CUtensorMap mapA, const __grid_constant__ C
     for (int tile = blockIdx.x; tile < P.ntiles && ok; tile += gridDim.x) {
       const TileWork w = decode_tile<MODE>(P, tile);
       if (w.nseg == 0) continue;
-      const int buf = lt % NBUF;
-      const uint32_t use = (uint32_t)(lt / NBUF);
-      // wait until the epilogue has drained this accumulator set
-      if (!tc::mbar_wait(&acce_bar[buf], (use & 1) ^ 1, abort_flag)) { ok = false; break; }
-      tc::tc_fence_after();
-      const uint32_t accbase = tmem + buf * BUF_COLS;
-      for (int si = 0; si < w.nseg && ok; ++si) {
-        const Segment& s = w.seg[si];
-        const uint32_t acc_hi = accbase + s.acc_col, acc_lo = accbase + s.acc_col + BN;
-        for (int ks = s.kbeg; ks < s.kend; ++ks, ++t) {
+      const Segment& s = w.seg[0];
+      // one accumulator use per chunk (MOMENT) or per tile (PAIR)
+      const int span = (MODE == MODE_MOMENT) ? CHUNK_STEPS : (s.kend - s.kbeg);
+      for (int kc = s.kbeg; kc < s.kend && ok; kc += span) {
+        const int kce = min(s.kend, kc + span);
+        const int buf = lt % NBUF;
+        const uint32_t use = (uint32_t)(lt / NBUF);
+        // wait until the epilogue has drained this accumulator set
+        if (!tc::mbar_wait(&acce_bar[buf], (use & 1) ^ 1, abort_flag)) { ok = false; break; }
+        tc::tc_fence_after();
+        const uint32_t acc_hi = tmem + buf * BUF_COLS + s.acc_col;
+        const uint32_t acc_lo = acc_hi + BN;
+        for (int ks = kc; ks < kce; ++ks, ++t) {
           const int st = t % STAGES;
           const uint32_t ph = (t / STAGES) & 1;
           if (!tc::mbar_wait(&full_bar[st], ph, abort_flag)) { ok = false; break; }
@@ -273,7 +285,7 @@ gemm6_kernel(const __grid_constant__ CUtensorMap mapA, const __grid_constant__ C
           const uint32_t base = tc::smem_u32(smem + st * STAGE_BYTES);
 #pragma unroll
           for (int kk = 0; kk < BK / 16; ++kk) {
-            const uint32_t acc = (ks > s.kbeg || kk > 0) ? 1u : 0u;
+            const uint32_t acc = (ks > kc || kk > 0) ? 1u : 0u;
 #pragma unroll
             for (int pi = 0; pi < 5; ++pi) {
               const uint64_t ad = tc::sdesc_sw64(base + pa[pi] * TILE_A + kk * 32);
@@ -286,10 +298,11 @@ gemm6_kernel(const __grid_constant__ CUtensorMap mapA, const __grid_constant__ C
           tc::umma_commit(&empty_bar[st]);
           consumed_sh = t + 1;
         }
+        if (!ok) break;
+        tc::umma_commit(&accf_bar[buf]);
+        committed_sh = lt + 1;
+        ++lt;
       }
-      tc::umma_commit(&accf_bar[buf]);
-      committed_sh = lt + 1;
-      ++lt;
     }
   } else if (warp >= 2) {
     // ---------------- epilogue ----------------
@@ -298,16 +311,17 @@ gemm6_kernel(const __grid_constant__ CUtensorMap mapA, const __grid_constant__ C
     const int r = qd * 32 + lane;
     const int col0 = half * (BN / 2);
     int lt = 0;
-    for (int tile = blockIdx.x; tile < P.ntiles; tile += gridDim.x) {
+    bool ok = true;
+    for (int tile = blockIdx.x; tile < P.ntiles && ok; tile += gridDim.x) {
       const TileWork w = decode_tile<MODE>(P, tile);
       if (w.nseg == 0) continue;
-      const int buf = lt % NBUF;
-      const uint32_t use = (uint32_t)(lt / NBUF);
-      if (!tc::mbar_wait(&accf_bar[buf], use & 1, abort_flag)) break;
-      tc::tc_fence_after();
-      const uint32_t trow = tmem + buf * BUF_COLS + ((uint32_t)(qd * 32) << 16);
       const int p = w.p0 + r;
       if (MODE == MODE_PAIR) {
+        const int buf = lt % NBUF;
+        const uint32_t use = (uint32_t)(lt / NBUF);
+        if (!__all_sync(0xffffffffu, tc::mbar_wait(&accf_bar[buf], use & 1, abort_flag))) break;
+        tc::tc_fence_after();
+        const uint32_t trow = tmem + buf * BUF_COLS + ((uint32_t)(qd * 32) << 16);
         // X[p][pair][orient][c] = (hi + lo) * unit(A row) * unit(B row), FP32
         const Segment& sg = w.seg[0];
         const bool prow = p < P.N;
@@ -340,29 +354,48 @@ gemm6_kernel(const __grid_constant__ CUtensorMap mapA, const __grid_constant__ C
           }
         }
 
+        // this accumulator set may be overwritten once every epilogue warp is done
+        tc::tc_fence_before();
+        __syncwarp();
+        if (lane == 0) tc::mbar_arrive(&acce_bar[buf]);
+        ++lt;
       } else {
-        double* U = P.U0 + (long long)w.moment * P.N * P.N;
-        const double uA = (p < P.N) ? (double)P.unitA[(long long)w.moment * P.N + p] : 0.0;
-        for (int cb = col0; cb < col0 + BN / 2; cb += 16) {
-          float hi[16], lo[16];
-          tc::tmem_ld16(trow + cb, hi);
-          tc::tmem_ld16(trow + BN + cb, lo);
-          if (p < P.N) {
+        // U^(n)[p][q] += u(p) u(q) sum over the tile's chunks of (hi + lo):
+        // chunks summed in FP32 registers, one FP64 atomic per element
+        const Segment& sg = w.seg[0];
+        float acc[BN / 2];
 #pragma unroll
-            for (int c = 0; c < 16; ++c) {
-              const int q = w.q0 + cb + c;
-              if (q < P.N)
-                atomicAdd(U + (long long)p * P.N + q,
-                          (double)(hi[c] + lo[c]) * (uA * (double)P.unitB[q]));
-            }
+        for (int c = 0; c < BN / 2; ++c) acc[c] = 0.f;
+        for (int kc = sg.kbeg; kc < sg.kend; kc += CHUNK_STEPS) {
+          const int buf = lt % NBUF;
+          const uint32_t use = (uint32_t)(lt / NBUF);
+          if (!__all_sync(0xffffffffu, tc::mbar_wait(&accf_bar[buf], use & 1, abort_flag))) { ok = false; break; }
+          tc::tc_fence_after();
+          const uint32_t trow = tmem + buf * BUF_COLS + ((uint32_t)(qd * 32) << 16);
+#pragma unroll
+          for (int g = 0; g < BN / 2; g += 16) {
+            float hi[16], lo[16];
+            tc::tmem_ld16(trow + col0 + g, hi);
+            tc::tmem_ld16(trow + BN + col0 + g, lo);
+#pragma unroll
+            for (int c = 0; c < 16; ++c) acc[g + c] += hi[c] + lo[c];
+          }
+          tc::tc_fence_before();
+          __syncwarp();
+          if (lane == 0) tc::mbar_arrive(&acce_bar[buf]);
+          ++lt;
+        }
+        if (!ok) break;
+        if (p < P.N) {
+          double* U = P.U0 + (long long)w.moment * P.N * P.N + (long long)p * P.N;
+          const double uA = (double)P.unitA[(long long)w.moment * P.N + p];
+#pragma unroll
+          for (int c = 0; c < BN / 2; ++c) {
+            const int q = w.q0 + col0 + c;
+            if (q < P.N) atomicAdd(U + q, (double)acc[c] * (uA * (double)P.unitB[q]));
           }
         }
       }
-      // this accumulator set may be overwritten once every epilogue warp is done
-      tc::tc_fence_before();
-      __syncwarp();
-      if (lane == 0) tc::mbar_arrive(&acce_bar[buf]);
-      ++lt;
     }
   }
 
@@ -372,53 +405,60 @@ gemm6_kernel(const __grid_constant__ CUtensorMap mapA, const __grid_constant__ C
     atomicExch(P.err, DEV_TIMEOUT);
     // let copies still in flight land before the shared memory goes away
     for (int t = consumed_sh; t < issued_sh; ++t) {
-      const long long t0 = clock64();
+      const unsigned long long t0 = tc::global_ns();
       while (!tc::mbar_try_wait(&full_bar[t % STAGES], (t / STAGES) & 1) &&
-             clock64() - t0 < tc::kWaitCycles) {
+             tc::global_ns() - t0 < tc::kWaitNs) {
       }
     }
   }
   if (warp == 1) {
     if (abort_sh && committed_sh > 0) {  // MMAs may still be running: wait for the last commit
       const int lt = committed_sh - 1;
-      const long long t0 = clock64();
+      const unsigned long long t0 = tc::global_ns();
       while (!tc::mbar_try_wait(&accf_bar[lt % NBUF], (uint32_t)((lt / NBUF) & 1)) &&
-             clock64() - t0 < tc::kWaitCycles) {
+             tc::global_ns() - t0 < tc::kWaitNs) {
       }
     }
+    __syncwarp();  // the bounded waits above may leave the lanes at different points
     tc::tc_fence_after();
     tc::tmem_dealloc(tmem, TMEM_COLS);
   }
 }
 
 // FP64 rows [nrow][ncol] (row stride ld) -> three BF16 limb planes
-// [3][nrow][ncolp] (zero padded to ncolp) in fixed point with the row's
-// power-of-two unit; also the unit and the Euclidean norm of each row.
-// One warp per row.
+// [3][dst_rows][ncolp] (zero padded to ncolp) in fixed point with the row's
+// certified power-of-two unit (tc::certified_unit: every h0 h0' partial sum of
+// the pair GEMM, K = the whole row, is exact).  Source row r lands in
+// destination row (r / grp) * gstride + goff + r % grp, which places a block
+// of rotated rows inside the full limb planes.  One warp per row.
 template <class T>
 __global__ void slice_rows_kernel(const T* __restrict__ src, long long nrow, int ncol,
-                                  long long ld, int ncolp, __nv_bfloat16* __restrict__ dst,
-                                  float* __restrict__ unit, double* __restrict__ norm) {
-  const long long plane = nrow * ncolp;
+                                  long long ld, int ncolp, long long dst_rows, long long grp,
+                                  long long gstride, long long goff,
+                                  __nv_bfloat16* __restrict__ dst, float* __restrict__ unit) {
+  const long long plane = dst_rows * ncolp;
   const int lane = threadIdx.x & 31;
   const long long nwarps = (long long)gridDim.x * (blockDim.x >> 5);
   for (long long r = (blockIdx.x * (long long)blockDim.x + threadIdx.x) >> 5; r < nrow;
        r += nwarps) {
     const T* row = src + r * ld;
-    double m = 0.0, ss = 0.0;
+    const long long dr = (r / grp) * gstride + goff + r % grp;
+    double m = 0.0, s2 = 0.0, s1 = 0.0;
     for (int c = lane; c < ncol; c += 32) {
-      const double x = row[c];
-      m = fmax(m, fabs(x));
-      ss = fma(x, x, ss);
+      const double x = fabs((double)row[c]);
+      m = fmax(m, x);
+      s2 = fma(x, x, s2);
+      s1 += x;
     }
 #pragma unroll
     for (int o = 16; o > 0; o >>= 1) {
       m = fmax(m, __shfl_xor_sync(0xffffffffu, m, o));
-      ss += __shfl_xor_sync(0xffffffffu, ss, o);
+      s2 += __shfl_xor_sync(0xffffffffu, s2, o);
+      s1 += __shfl_xor_sync(0xffffffffu, s1, o);
     }
-    const double u = tc::slice_unit(m);
+    const double u = tc::certified_unit(m, s2, s1, (double)ncolp);
     const double inv = 1.0 / u;  // exact: u is a power of two
-    __nv_bfloat16* d = dst + r * ncolp;
+    __nv_bfloat16* d = dst + dr * ncolp;
     for (int c = lane; c < ncolp; c += 32) {
       const double x = (c < ncol) ? (double)row[c] : 0.0;
       __nv_bfloat16 h0, h1, h2;
@@ -427,10 +467,7 @@ __global__ void slice_rows_kernel(const T* __restrict__ src, long long nrow, int
       d[plane + c] = h1;
       d[2 * plane + c] = h2;
     }
-    if (lane == 0) {
-      unit[r] = (float)u;
-      if (norm) norm[r] = sqrt(ss);
-    }
+    if (lane == 0) unit[dr] = (float)u;
   }
 }
 
@@ -485,7 +522,7 @@ __global__ void __launch_bounds__(256) combine_kernel(const Combine C) {
     iu[n] = 1.f;
     mx[n] = 0.f;
     if (PASS == 1 && n < C.nm)
-      iu[n] = 1.0f / tc::slice_unitf(__uint_as_float(C.maxbits[(long long)n * C.N + p]));
+      iu[n] = 1.0f / tc::slice_unitf(__uint_as_float(C.maxbits[(long long)n * C.N + p]), 8);
   }
   const float* xr = C.X + (long long)p * C.xrow;
   for (int e = blockIdx.x * blockDim.x + threadIdx.x; e < total; e += gridDim.x * blockDim.x) {
@@ -558,7 +595,7 @@ __global__ void __launch_bounds__(256) combine_kernel(const Combine C) {
     }
   } else if (blockIdx.x == 0 && threadIdx.x < C.nm) {
     C.unit[(long long)threadIdx.x * C.N + p] =
-        tc::slice_unitf(__uint_as_float(C.maxbits[(long long)threadIdx.x * C.N + p]));
+        tc::slice_unitf(__uint_as_float(C.maxbits[(long long)threadIdx.x * C.N + p]), 8);
   }
 }
 
@@ -615,7 +652,8 @@ struct Buffers {
 
 struct MixedWs {
   Buffers lx_o, lx_v, l_ov, y, pairs, err;
-  Buffers u_xo, u_xv, u_ov, u_y, x32, maxbits;
+  Buffers u_xo, u_xv, u_ov, u_y, x32, maxbits, rot;
+  Buffers l4, u_l4, co4, cv4, u_co, u_cv, rot_stats, w4, u_w4, rot_ov;
 };
 
 std::mutex g_attr_mu;
@@ -647,15 +685,16 @@ void mixed_workspace_destroy(void* w) {
   if (!w) return;
   MixedWs* W = static_cast<MixedWs*>(w);
   for (Buffers* b : {&W->lx_o, &W->lx_v, &W->l_ov, &W->y, &W->pairs, &W->err, &W->u_xo,
-                     &W->u_xv, &W->u_ov, &W->u_y, &W->x32, &W->maxbits})
+                     &W->u_xv, &W->u_ov, &W->u_y, &W->x32, &W->maxbits, &W->rot, &W->l4, &W->u_l4, &W->co4,
+                     &W->cv4, &W->u_co, &W->u_cv, &W->rot_stats, &W->w4, &W->u_w4, &W->rot_ov})
     if (b->p) cudaFree(b->p);
   delete W;
 }
 
-int mixed_build_moments_rotated(const double* Lxo, const double* Lxv, const double* Lov, int naux,
-                                int N, int o, int v, const double* eo, const double* ev, int nmom,
-                                double* U_hole, double* U_part, std::string& err,
-                                cudaStream_t s, KernelStats* stats, void* workspace) {
+int mixed_build_moments(const double* L, int naux, int N, const double* Co, const double* Cv,
+                        int o, int v, const double* eo, const double* ev, int nmom,
+                        double* U_hole, double* U_part, std::string& err, cudaStream_t s,
+                        KernelStats* stats, void* workspace) {
   // CUDA events around the tcgen05 launches when stats->enabled
   std::vector<cudaEvent_t> evs;
   std::vector<int> ev_kind;
@@ -711,17 +750,75 @@ int mixed_build_moments_rotated(const double* Lxo, const double* Lxv, const doub
   const int nm = nmom + 1;
   float* u_y = grow<float>(W.u_y, (size_t)nm * N, err);
   if (!u_xo || !u_xv || !u_ov || !u_y) return AGF2_ERR_OOM;
-  // rotated FP64 tensors have layout [x][p][Q] / [j][a][Q] with row length naux
-  auto slice = [&](auto* src, long long rows, int ncol, long long ld, int ncolp,
-                   __nv_bfloat16* dst, float* unit) {
-    const long long blocks = std::min<long long>((rows + 7) / 8, 152LL * 16);
-    slice_rows_kernel<<<(int)std::max(1LL, blocks), 256, 0, s>>>(src, rows, ncol, ld, ncolp, dst,
-                                                                 unit, (double*)nullptr);
-    count_launch();
-  };
-  slice(Lxo, (long long)o * N, naux, naux, Qs, lxo, u_xo);
-  slice(Lxv, (long long)v * N, naux, naux, Qs, lxv, u_xv);
-  slice(Lov, (long long)o * v, naux, naux, Qs, lov, u_ov);
+  // ---- a2: rotation into the pole basis on the tensor cores ----
+  // Lxo[i][p][Q] = sum_r Co[r][i] L[Q][r][p] and Lxv likewise, one block of
+  // outer poles at a time through W[x][Q][p] = sum_r Cx[r][x] L[Q][p][r]
+  // (batched over Q, p contiguous), which a transposing slicer turns into the
+  // limb planes of the rows (x, p) over Q; Lov[j][a][Q] = sum_p Co[p][j]
+  // W_v[a][Q][p] (batched over a, Q contiguous).  Four-limb integer splits
+  // with exactly summed 256-entry chunks (rotate.cu) keep the rotated values
+  // FP64-class, so the three-limb slicing of the result stays the only
+  // precision step before the pair GEMM.  Only the limbs of the three
+  // rotated tensors are held whole.
+  {
+    const int Ns = (N + 255) / 256 * 256;  // K of the rotation GEMMs (r or p)
+    const long long nQN = (long long)naux * N;
+    __nv_bfloat16* l4 = grow<__nv_bfloat16>(W.l4, 4LL * nQN * Ns, err);
+    float* u_l4 = grow<float>(W.u_l4, (size_t)nQN, err);
+    __nv_bfloat16* co4 = grow<__nv_bfloat16>(W.co4, 4LL * o * Ns, err);
+    __nv_bfloat16* cv4 = grow<__nv_bfloat16>(W.cv4, 4LL * v * Ns, err);
+    float* u_co = grow<float>(W.u_co, (size_t)o, err);
+    float* u_cv = grow<float>(W.u_cv, (size_t)v, err);
+    if (!l4 || !u_l4 || !co4 || !cv4 || !u_co || !u_cv) return AGF2_ERR_OOM;
+    int rc;
+    // rows (Q, p) of L over r; rows x of C^T over r (C is [N][x])
+    if ((rc = rot_limbs_slice4(L, nQN, N, N, 1, Ns, nQN, nQN, 0, 0, l4, u_l4, s)) ||
+        (rc = rot_limbs_slice4(Co, o, N, 1, o, Ns, o, o, 0, 0, co4, u_co, s)) ||
+        (rc = rot_limbs_slice4(Cv, v, N, 1, v, Ns, v, v, 0, 0, cv4, u_cv, s))) {
+      err = "rotation slicing launch failed";
+      return rc;
+    }
+    // per outer pole: W [nQ][N] FP64; per virtual pole also its four-limb
+    // planes [nQ][Ns] and its Lov column block [o][nQ] FP64
+    const size_t budget = size_t(4) << 30;
+    const long long per_o = nQN * 8;
+    const long long per_v = nQN * 8 + 4LL * naux * Ns * 2 + (long long)o * naux * 8;
+    const int bi = (int)std::max<long long>(1, std::min<long long>(o, budget / per_o));
+    const int ba = (int)std::max<long long>(1, std::min<long long>(v, budget / per_v));
+    double* wtmp = grow<double>(W.rot, (size_t)std::max<long long>((long long)bi, ba) * nQN, err);
+    double* stats = grow<double>(W.rot_stats, 3 * (size_t)std::max(bi, ba) * N, err);
+    __nv_bfloat16* w4 = grow<__nv_bfloat16>(W.w4, 4LL * ba * naux * Ns, err);
+    float* u_w4 = grow<float>(W.u_w4, (size_t)ba * naux, err);
+    double* tmpov = grow<double>(W.rot_ov, (size_t)o * ba * naux, err);
+    if (!wtmp || !stats || !w4 || !u_w4 || !tmpov) return AGF2_ERR_OOM;
+    for (int i0 = 0; i0 < o; i0 += bi) {
+      const int nb = std::min(bi, o - i0);
+      if ((rc = rot_gemm4(co4, o, i0, nb, u_co, l4, N, naux, u_l4, Ns, wtmp, nQN, N, derr, err,
+                          s)) ||
+          (rc = rot_transpose_slice3(wtmp, nb, naux, N, Qs, stats, (long long)o * N,
+                                     (long long)i0 * N, lxo, u_xo, s)))
+        return rc ? rc : AGF2_ERR_CUDA;
+    }
+    for (int a0 = 0; a0 < v; a0 += ba) {
+      const int nb = std::min(ba, v - a0);
+      if ((rc = rot_gemm4(cv4, v, a0, nb, u_cv, l4, N, naux, u_l4, Ns, wtmp, nQN, N, derr, err,
+                          s)) ||
+          (rc = rot_transpose_slice3(wtmp, nb, naux, N, Qs, stats, (long long)v * N,
+                                     (long long)a0 * N, lxv, u_xv, s)))
+        return rc ? rc : AGF2_ERR_CUDA;
+      // rows (a, Q) of W_v over p, then tmpov[j][a'][Q] = sum_p Co[p][j] W_v[a'][Q][p]
+      const long long rows = (long long)nb * naux;
+      if ((rc = rot_limbs_slice4(wtmp, rows, N, N, 1, Ns, rows, rows, 0, 0, w4, u_w4, s)) ||
+          (rc = rot_gemm4(co4, o, 0, o, u_co, w4, naux, nb, u_w4, Ns, tmpov,
+                          (long long)nb * naux, naux, derr, err, s)))
+        return rc ? rc : AGF2_ERR_CUDA;
+      // row (j, a') of the block is row j v + a0 + a' of the Lov planes
+      const long long blocks = std::min<long long>(((long long)o * nb + 7) / 8, 152LL * 16);
+      slice_rows_kernel<<<(int)std::max(1LL, blocks), 256, 0, s>>>(
+          tmpov, (long long)o * nb, naux, naux, Qs, (long long)o * v, nb, v, a0, lov, u_ov);
+      count_launch();
+    }
+  }
   if (cudaGetLastError() != cudaSuccess) {
     err = "slice kernel launch failed";
     return AGF2_ERR_CUDA;
@@ -766,17 +863,19 @@ int mixed_build_moments_rotated(const double* Lxo, const double* Lxv, const doub
     const int ncp = n_cchunks * BN;
     const long long kpp = (long long)n_cchunks * KCHUNK;
     // pairs per block: large enough that GEMM 2's split-K tiles are long (each
-    // tile ends in a 128x128 FP64 drain), about 256 MB of X + Y + Yw, and a
-    // whole number of waves of the persistent CTAs
+    // tile ends in a 128x128 FP64 drain) and launches few, about 1 GB of X + Y
+    // + Yw (measured at nmo = 200 / 500: 0.26 / 0.25 GB blocks 15% / 10% slower
+    // in GEMM 2, 2 GB no faster), and a whole number of waves of the
+    // persistent CTAs
     const double per_pair = (double)N * (kpp * nm /*Y w^n*/ * 3 /*limbs*/ * 2 /*bytes*/ +
                                          2.0 * ncp * 4 /*X, both orders*/);
     const int tpp = 2 * n_ptiles * n_cchunks;  // tiles per unordered pair
-    int bp = (int)std::max(1.0, std::floor(256.0e6 / per_pair));
+    int bp = (int)std::max(1.0, std::floor(1.0e9 / per_pair));
     {
       int g = nsm, t = tpp;
       while (t) { const int r = g % t; g = t; t = r; }  // gcd(nsm, tpp)
       const int unit = nsm / g;                          // pairs per whole wave
-      const int bp_lim = (int)std::floor(384.0e6 / per_pair);
+      const int bp_lim = (int)std::floor(1.5e9 / per_pair);
       if (unit <= bp_lim) bp = std::max(unit, bp / unit * unit);
     }
     bp = std::max(1, std::min<int>(bp, (int)pairs.size()));
@@ -842,10 +941,13 @@ int mixed_build_moments_rotated(const double* Lxo, const double* Lxv, const doub
       M.ksteps = (int)((K + BK - 1) / BK);
       M.nm = nm;
       const int tiles = M.n_ptiles * (M.n_ptiles + 1) / 2 * nm;  // upper tiles x moments
-      // about two tiles per persistent CTA, so each drain overlaps the next tile's MMAs
+      // about two tiles per persistent CTA, so each tile's atomics overlap the
+      // next tile's MMAs; splits on chunk boundaries, at most MAX_TILE_CHUNKS each
+      const int nchunks = M.ksteps / CHUNK_STEPS;  // K is a whole number of chunks
       int nsplit = std::max(1, (nsm * 2 + tiles - 1) / tiles);
-      nsplit = std::min(nsplit, M.ksteps);
-      M.ksplit = (M.ksteps + nsplit - 1) / nsplit;
+      nsplit = std::max(nsplit, (nchunks + MAX_TILE_CHUNKS - 1) / MAX_TILE_CHUNKS);
+      nsplit = std::min(nsplit, nchunks);
+      M.ksplit = (nchunks + nsplit - 1) / nsplit * CHUNK_STEPS;
       M.nsplit = (M.ksteps + M.ksplit - 1) / M.ksplit;  // every split non-empty
       M.ntiles = tiles * M.nsplit;
       M.n_out = 0;

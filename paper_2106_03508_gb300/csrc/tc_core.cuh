@@ -17,8 +17,16 @@
 namespace agf2 {
 namespace tc {
 
-// Wait limit, in SM clock cycles (~2 s at 2 GHz).
-constexpr long long kWaitCycles = 4000000000LL;
+// Wait limit, in ns of the global timer (2 s).  The global timer is the time
+// base of every bounded wait: a thread suspended in mbarrier.try_wait or in
+// a sleep does not keep an SM-clock counter advancing at its nominal rate.
+constexpr unsigned long long kWaitNs = 2000000000ULL;
+
+__device__ __forceinline__ unsigned long long global_ns() {
+  unsigned long long t;
+  asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+  return t;
+}
 
 __device__ __forceinline__ uint32_t smem_u32(const void* p) {
   return static_cast<uint32_t>(__cvta_generic_to_shared(p));
@@ -58,10 +66,10 @@ __device__ __forceinline__ bool mbar_try_wait(uint64_t* bar, uint32_t parity) {
 // Bounded wait for the phase with the given parity.  Returns false (and sets
 // *abort) if the CTA is aborting or the limit is reached.
 __device__ __forceinline__ bool mbar_wait(uint64_t* bar, uint32_t parity, volatile int* abort) {
-  const long long t0 = clock64();
+  const unsigned long long t0 = global_ns();
   while (!mbar_try_wait(bar, parity)) {
     if (*abort) return false;
-    if (clock64() - t0 > kWaitCycles) {
+    if (global_ns() - t0 > kWaitNs) {
       *abort = 1;
       return false;
     }
@@ -183,6 +191,30 @@ __device__ __forceinline__ void tmem_ld32(uint32_t taddr, float* v) {
   for (int i = 0; i < 32; ++i) v[i] = __uint_as_float(r[i]);
 }
 
+// 4 consecutive FP32 columns of this thread's TMEM lane.
+__device__ __forceinline__ void tmem_ld4(uint32_t taddr, float* v) {
+  uint32_t r[4];
+  asm volatile("tcgen05.ld.sync.aligned.32x32b.x4.b32 {%0, %1, %2, %3}, [%4];"
+               : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3])
+               : "r"(taddr));
+  asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+#pragma unroll
+  for (int i = 0; i < 4; ++i) v[i] = __uint_as_float(r[i]);
+}
+
+// 8 consecutive FP32 columns of this thread's TMEM lane.
+__device__ __forceinline__ void tmem_ld8(uint32_t taddr, float* v) {
+  uint32_t r[8];
+  asm volatile(
+      "tcgen05.ld.sync.aligned.32x32b.x8.b32 {%0, %1, %2, %3, %4, %5, %6, %7}, [%8];"
+      : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]),
+        "=r"(r[7])
+      : "r"(taddr));
+  asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+#pragma unroll
+  for (int i = 0; i < 8; ++i) v[i] = __uint_as_float(r[i]);
+}
+
 // 16 consecutive FP32 columns of this thread's TMEM lane.
 __device__ __forceinline__ void tmem_ld16(uint32_t taddr, float* v) {
   uint32_t r[16];
@@ -199,12 +231,15 @@ __device__ __forceinline__ void tmem_ld16(uint32_t taddr, float* v) {
 }
 
 // ---- fixed-point three-limb BF16 slicing ----
-// With a per-row power-of-two unit s (|x| <= 256 s on that row),
-//   x / s ~ h0 + h1 + h2,  h0 integer in [-256, 256], h1 in 2^-8 Z,
+// With a per-row power-of-two unit s (|x| < R s on that row, R = 2^rbits,
+// rbits <= 8),
+//   x / s ~ h0 + h1 + h2,  h0 an integer in [-R, R], h1 in 2^-8 Z,
 //   h2 in 2^-16 Z (|h1|, |h2| <= 128 units of their grid),
-// all exactly representable in BF16.  Products h0*h0' are integers below
-// 2^16, so their FP32 tensor-core accumulation is exact until |sum| reaches
-// 2^24; the remaining limb products are kept in a separate accumulator.
+// all exactly representable in BF16.  Products h0*h0' are integers of
+// magnitude <= R^2, so a sum of K of them is exact in the FP32 tensor-core
+// accumulator whenever R^2 K <= 2^24; the caller picks rbits from the
+// accumulation length (hi_bits).  The remaining limb products are kept in a
+// separate accumulator.
 __device__ __forceinline__ void slice3(double u, __nv_bfloat16& h0, __nv_bfloat16& h1,
                                        __nv_bfloat16& h2) {
   const double a0 = rint(u);
@@ -227,20 +262,35 @@ __device__ __forceinline__ void slice3f(float u, __nv_bfloat16& h0, __nv_bfloat1
   h2 = __float2bfloat16_rn(a2 * (1.0f / 65536.0f));
 }
 
-// FP32 variant of slice_unit.
-__device__ __forceinline__ float slice_unitf(float m) {
-  if (!(m > 0.0f)) return 1.0f;
-  int E;
-  frexpf(m, &E);
-  return ldexpf(1.0f, E - 8);
-}
-
-// Smallest power of two 2^E with m < 2^E, returned as the slicing unit 2^(E-8).
-__host__ __device__ __forceinline__ double slice_unit(double m) {
+// Slicing unit of a row with max |x| = m: the power of two 2^(E - rbits)
+// with m < 2^E, so that |x| / unit < 2^rbits.
+__host__ __device__ __forceinline__ double slice_unit(double m, int rbits) {
   if (!(m > 0.0)) return 1.0;
   int E;
   frexp(m, &E);  // m = f 2^E, f in [0.5, 1)
-  return ldexp(1.0, E - 8);
+  return ldexp(1.0, E - rbits);
+}
+
+__device__ __forceinline__ float slice_unitf(float m, int rbits) {
+  if (!(m > 0.0f)) return 1.0f;
+  int E;
+  frexpf(m, &E);
+  return ldexpf(1.0f, E - rbits);
+}
+
+// Row unit with an exactness certificate: start from slice_unit(m, 8) and
+// double it until sum_k (|x_k|/u + 1/2)^2 <= 2^24, bounded above by
+// s2/u^2 + s1/u + n/4 (s2 = sum x^2, s1 = sum |x|, n entries).  Then the
+// row's integer limbs satisfy sum_k h0_k^2 <= 2^24, so by Cauchy-Schwarz
+// every partial sum of h0 h0' products between two such rows -- over any
+// K range -- is an integer of magnitude <= 2^24, exact in FP32.  Doubling
+// the unit is needed only for rows whose entries are nearly all of the
+// row's maximum size, where a coarser grid costs little.
+__host__ __device__ __forceinline__ double certified_unit(double m, double s2, double s1,
+                                                          double n) {
+  double u = slice_unit(m, 8);
+  while (s2 / (u * u) + s1 / u + 0.25 * n > 16777216.0) u *= 2.0;
+  return u;
 }
 
 }  // namespace tc

@@ -19,6 +19,10 @@ def test_dominant_kernel_and_rooflines():
     t = roofs[0]
     assert t["bound"] == "tensor" and t["peak"] == 1700.0
     assert abs(t["achieved"] - 170.0) < 1e-9 and abs(t["issued_tflops"] - 1020.0) < 1e-9
+    # with a measured FP64 GEMM rate, the FP64 kinds are measured against it
+    dom, roofs = bench.kernel_rooflines(stats, 5, peaks, "measured", fp64_peak=1.1)
+    assert roofs[2]["peak"] == 1.1 and abs(roofs[2]["frac"] - roofs[2]["achieved"] / 1.1) < 1e-12
+    assert "measured" in roofs[2]["peak_source"]
     # nothing timed: zero rates, no division by zero
     dom0, roofs0 = bench.kernel_rooflines({k: (0, 0.0, 0.0) for k in range(4)}, 1, peaks, "m")
     assert all(roofs0[k]["achieved"] == 0.0 for k in range(4))
@@ -31,3 +35,13 @@ def test_steady_state_pole_counts():
         N = CONFIGS["c1"]["nmo"]
         assert o + v == (nmom + 2) * N
         assert o == CONFIGS["c1"]["nocc"] + (nmom + 1) // 2 * N
+
+
+def test_oracle_sample_scales_both_sectors():
+    """The CPU-baseline sample times a share of both outer summed indices plus
+    one Fock cycle and extrapolates to one iteration: on the small c1 system
+    the estimate exceeds the sample's own wall time and the description names
+    both sectors."""
+    t_iter, wall, desc = bench.oracle_sample("c1", 1, fock_cycles=3, frac=0.25)
+    assert t_iter > 0 and wall > 0
+    assert "occupied" in desc and "virtual" in desc and "x 3 cycles" in desc

@@ -21,7 +21,7 @@ def test_batched_uneven_systems_match_oracle(cuda_handle, agf2_lib):
         refs.append(O.run(h, s.L, s.nelec, s.eps, max_iter=30))
         L, hc, eps = (torch.from_numpy(np.ascontiguousarray(x)).cuda() for x in (s.L, h, s.eps))
         keep += [L, hc, eps]
-        systems.append((hc.data_ptr(), L.data_ptr(), eps.data_ptr(), naux, nmo, s.nelec))
+        systems.append((hc.data_ptr(), L.data_ptr(), None, naux, nmo, s.nelec))
     o = agf2_lib.agf2_opts_default()
     o.max_iter = 30
     rc, outs, st = agf2_lib.agf2_run_batched(cuda_handle.h, systems, o, nworkers=3)

@@ -32,7 +32,7 @@ def trajectory(lib, h, precision, nit=NIT, shift_mode=0):
     for it in range(nit):
         o.resume = 1 if it else 0
         rc, r = lib.agf2_run(h.h, hc.data_ptr(), L.data_ptr(), s.naux, s.nmo, s.nelec,
-                             eps.data_ptr(), o)
+                             None, o)
         out.append(r.as_dict())
     return out
 

@@ -124,7 +124,7 @@ def run_gpu(lib, h, s, nmom, nit, precision=0, shift_mode=1):
     for it in range(nit):
         o.resume = 1 if it else 0
         rc, r = lib.agf2_run(h.h, hc.data_ptr(), L.data_ptr(), s.naux, s.nmo, s.nelec,
-                             eps.data_ptr(), o)
+                             None, o)
         out.append(r.as_dict())
     return out
 

@@ -42,7 +42,8 @@ def test_run_iteration_cap(cuda_handle, agf2_lib):
     o.max_iter = 2
     o.conv_tol = 0.0  # |dE| < 0 never holds
     rc, out = agf2_lib.agf2_run(cuda_handle.h, hd.data_ptr(), L.data_ptr(), s.naux, s.nmo,
-                                s.nelec, eps.data_ptr(), o)
+                                s.nelec, None, o)
     assert rc == agf2_lib.AGF2_ERR_NO_CONVERGENCE
     assert out.iterations == 2 and out.converged == 0
     assert np.isfinite(out.E_tot) and np.isfinite(out.ip) and np.isfinite(out.ea)
+

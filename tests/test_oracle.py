@@ -302,6 +302,42 @@ def test_slice_additivity():
     assert rel(ph, bh) < 1e-12 and rel(pq, bp) < 1e-12
     # a genuine slice: it is neither zero nor the whole
     assert 0.05 < np.max(np.abs(ph)) / np.max(np.abs(Uh)) < 0.95
+    # slices of the first summed index (i for the hole sector, a for the
+    # particle sector) of the per-index form partition the sums as well, and
+    # one slice is the explicit sum over the ordered pairs starting there
+    Th, Tp = np.zeros_like(Uh), np.zeros_like(Up)
+    for part in (([0, 3], [1, 4, 6]), ([1], [0, 5]), ([2], [2, 3])):
+        ph, pq = O.build_moments(s.L, e, C, mu, 1, outer_occ=part[0], outer_vir=part[1])
+        Th += ph
+        Tp += pq
+    assert rel(Th, Uh) < 1e-13 and rel(Tp, Up) < 1e-13
+    ph, pq = O.build_moments(s.L, e, C, mu, 1, outer_occ=[1], outer_vir=[4])
+    bh, _ = _ordered_first_loops(s.L, e, C, mu, [1], [])
+    _, bp = _ordered_first_loops(s.L, e, C, mu, [], [4])
+    assert rel(ph, bh) < 1e-12 and rel(pq, bp) < 1e-12
+
+
+def _ordered_first_loops(L, e, C, mu, first_occ, first_vir, nmom=1):
+    """Brute force: the moment sums restricted to outer pairs whose first
+    index is listed (positions in the occupied / virtual pole lists)."""
+    N = L.shape[1]
+    occ = [x for x in range(len(e)) if e[x] < mu]
+    vir = [x for x in range(len(e)) if not e[x] < mu]
+    g = O.pole_eris(L, C)
+    out = []
+    for first, outer, inner in ((first_occ, occ, vir), (first_vir, vir, occ)):
+        U = np.zeros((nmom + 1, N, N))
+        for p in range(N):
+            for q in range(N):
+                for xi in first:
+                    i = outer[xi]
+                    for j in outer:
+                        for c in inner:
+                            t = g[p, i, j, c] * (2.0 * g[q, i, j, c] - g[q, j, i, c])
+                            for n in range(nmom + 1):
+                                U[n, p, q] += t * (e[i] + e[j] - e[c]) ** n
+        out.append(0.5 * (U + U.transpose(0, 2, 1)))
+    return out
 
 
 def _eri(L):
@@ -485,3 +521,21 @@ def test_compression_independent_of_the_factor_of_u0():
             sig = (v / (w - E)) @ v.T
             sig_s = (vs / (w - Es)) @ vs.T
             assert rel(sig, sig_s) < 1e-9
+
+
+def test_run_general_basis_start_matches_canonical():
+    """Started from eig(F[D0]) in a rotated orbital basis (hcore, every L^Q and
+    D0 rotated by one orthogonal matrix), the iteration is the same physics as
+    the canonical-basis start: energies, IP and EA agree."""
+    s = make_system(8, 3, 10, 30)
+    L = 0.3 * s.L
+    h = O.hcore_from_mo_energies(s.eps, L, s.nocc)
+    rng = np.random.default_rng(2)
+    Qm, _ = np.linalg.qr(rng.standard_normal((8, 8)))
+    hr = Qm.T @ h @ Qm
+    Lr = np.einsum("pi,Qpq,qj->Qij", Qm, L, Qm)
+    D0r = Qm.T @ O.hf_density(8, 3) @ Qm
+    a = O.run(h, L, s.nelec, s.eps, max_iter=3, conv_tol=0.0, fock_tol=1e-12)
+    b = O.run(hr, Lr, s.nelec, None, max_iter=3, conv_tol=0.0, fock_tol=1e-12, D0=D0r)
+    for key in ("E_hf", "E_1b", "E_2b", "E_tot", "ip", "ea", "mu"):
+        assert abs(getattr(a, key) - getattr(b, key)) <= 1e-9 * max(1.0, abs(getattr(a, key))), key
