@@ -46,7 +46,9 @@ def parse():
     ap.add_argument("--config", default="c2")
     ap.add_argument("--precision", default="bf16x3", choices=["bf16x3", "fp64"])
     ap.add_argument("--fp64-steps", type=int, default=1,
-                    help="FP64-path iterations timed after the main steps (0: skip)")
+                    help="FP64-path iterations timed after the main steps, with the "
+                         "steady-state moment comparison; 0: only the iteration-1 "
+                         "comparison from the Hartree-Fock reference; -1: no FP64 leg")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--shift-mode", type=int, default=1, choices=[0, 1],
                     help="Fock-loop shift: 0 solve every cycle, 1 one Newton step per cycle")
@@ -427,46 +429,56 @@ def run_ours(args):
     #     state: FP64 time per iteration; (3) iteration 1 from the Hartree-Fock
     #     reference in each precision: E_tot, IP, EA differences.
     fp64 = None
-    if args.fp64_steps > 0 and prec != agf2.AGF2_FP64:
-        nq = agf2.agf2_get_state(h.h)
-        e_st = torch.empty(nq, dtype=torch.float64, device="cuda")
-        C_st = torch.empty(N, nq, dtype=torch.float64, device="cuda")
-        agf2.agf2_get_state(h.h, e=e_st.data_ptr(), C=C_st.data_ptr())
-        mu_st = results[-1]["mu"]
-        nm = args.nmom + 1
-        U, t_mom = {}, {}
-        for pname, pc in (("mixed", agf2.AGF2_BF16X3), ("fp64", agf2.AGF2_FP64)):
-            Uh = torch.empty(nm, N, N, dtype=torch.float64, device="cuda")
-            Up = torch.empty_like(Uh)
+    if args.fp64_steps >= 0 and prec != agf2.AGF2_FP64:
+        fp64 = {}
+        if args.fp64_steps > 0:
+            nq = agf2.agf2_get_state(h.h)
+            e_st = torch.empty(nq, dtype=torch.float64, device="cuda")
+            C_st = torch.empty(N, nq, dtype=torch.float64, device="cuda")
+            agf2.agf2_get_state(h.h, e=e_st.data_ptr(), C=C_st.data_ptr())
+            mu_st = results[-1]["mu"]
+            nm = args.nmom + 1
+            U, t_mom = {}, {}
+            for pname, pc in (("mixed", agf2.AGF2_BF16X3), ("fp64", agf2.AGF2_FP64)):
+                Uh = torch.empty(nm, N, N, dtype=torch.float64, device="cuda")
+                Up = torch.empty_like(Uh)
+                barrier()
+                t0 = time.perf_counter()
+                agf2.agf2_build_moments(h.h, L.data_ptr(), naux, N, e_st.data_ptr(),
+                                        C_st.data_ptr(), nq, mu_st, args.nmom, pc, Uh.data_ptr(),
+                                        Up.data_ptr())
+                barrier()
+                t_mom[pname] = time.perf_counter() - t0
+                U[pname] = (Uh.cpu(), Up.cpu())
+            moment_err = {}
+            for si, sec in enumerate(("hole", "particle")):
+                for n in range(nm):
+                    ref = U["fp64"][si][n]
+                    moment_err[f"{sec}_U{n}"] = float((U["mixed"][si][n] - ref).abs().max() /
+                                                      ref.abs().max())
+            of = agf2.agf2_opts_default()
+            of.precision = agf2.AGF2_FP64
+            of.nmom = args.nmom
+            of.fock.shift_mode = args.shift_mode
+            of.max_iter = 1
+            of.resume = 1
             barrier()
             t0 = time.perf_counter()
-            agf2.agf2_build_moments(h.h, L.data_ptr(), naux, N, e_st.data_ptr(),
-                                    C_st.data_ptr(), nq, mu_st, args.nmom, pc, Uh.data_ptr(),
-                                    Up.data_ptr())
+            fr = []
+            for _ in range(args.fp64_steps):
+                rc, out = agf2.agf2_run(h.h, hc.data_ptr(), L.data_ptr(), naux, N, nelec,
+                                        None, of)
+                fr.append(out.as_dict())
             barrier()
-            t_mom[pname] = time.perf_counter() - t0
-            U[pname] = (Uh.cpu(), Up.cpu())
-        moment_err = {}
-        for si, sec in enumerate(("hole", "particle")):
-            for n in range(nm):
-                ref = U["fp64"][si][n]
-                moment_err[f"{sec}_U{n}"] = float((U["mixed"][si][n] - ref).abs().max() /
-                                                  ref.abs().max())
-        of = agf2.agf2_opts_default()
-        of.precision = agf2.AGF2_FP64
-        of.nmom = args.nmom
-        of.fock.shift_mode = args.shift_mode
-        of.max_iter = 1
-        of.resume = 1
-        barrier()
-        t0 = time.perf_counter()
-        fr = []
-        for _ in range(args.fp64_steps):
-            rc, out = agf2.agf2_run(h.h, hc.data_ptr(), L.data_ptr(), naux, N, nelec,
-                                    None, of)
-            fr.append(out.as_dict())
-        barrier()
-        dt = (time.perf_counter() - t0) / args.fp64_steps
+            dt = (time.perf_counter() - t0) / args.fp64_steps
+            fp64.update({
+                "iterations_per_s": 1.0 / dt, "s_per_iter": dt,
+                "moment_s": t_mom["fp64"], "mixed_moment_s": t_mom["mixed"],
+                "moment_tflops": statistics.mean(r["flops_moments"] / r["t_moments"] / 1e12
+                                                 for r in fr),
+                "mixed_speedup_per_iter": (args.steps / elapsed) * dt,
+                "mixed_speedup_moment_build": t_mom["fp64"] / t_mom["mixed"],
+                "moment_max_rel_err_vs_fp64": moment_err})
         it1 = {}
         for pname, pc in (("mixed", agf2.AGF2_BF16X3), ("fp64", agf2.AGF2_FP64)):
             o1 = agf2.agf2_opts_default()
@@ -475,25 +487,20 @@ def run_ours(args):
             o1.fock.shift_mode = args.shift_mode
             o1.max_iter = 1
             o1.resume = 0
-            rc, out = agf2.agf2_run(h.h, hc.data_ptr(), L.data_ptr(), naux, N, nelec,
-                                    None, o1)
+            t0 = time.perf_counter()
+            rc, out = agf2.agf2_run(h.h, hc.data_ptr(), L.data_ptr(), naux, N, nelec, None, o1)
             it1[pname] = out.as_dict()
-        fp64 = {"iterations_per_s": 1.0 / dt, "s_per_iter": dt,
-                "moment_s": t_mom["fp64"], "mixed_moment_s": t_mom["mixed"],
-                "moment_tflops": statistics.mean(r["flops_moments"] / r["t_moments"] / 1e12
-                                                 for r in fr),
-                "mixed_speedup_per_iter": (args.steps / elapsed) * dt,
-                "mixed_speedup_moment_build": t_mom["fp64"] / t_mom["mixed"],
-                "moment_max_rel_err_vs_fp64": moment_err,
-                "iteration1_from_hf": {
-                    "abs_diff_Ha": {k: abs(it1["mixed"][k] - it1["fp64"][k])
-                                    for k in ("E_tot", "E_2b", "ip", "ea")},
-                    "fp64": {k: it1["fp64"][k] for k in ("E_tot", "ip", "ea", "fock_cycles",
-                                                         "fock_converged")},
-                    "mixed": {k: it1["mixed"][k] for k in ("fock_cycles", "fock_converged")},
-                    "note": "a Fock loop stopped at its cycle cap unconverged ends where its "
-                            "own dynamics take it: differences then measure that sensitivity, "
-                            "not the moment error"}}
+            it1[pname]["wall_s"] = time.perf_counter() - t0
+        fp64["iteration1_from_hf"] = {
+            "abs_diff_Ha": {k: abs(it1["mixed"][k] - it1["fp64"][k])
+                            for k in ("E_tot", "E_2b", "ip", "ea")},
+            "fp64": {k: it1["fp64"][k] for k in ("E_tot", "ip", "ea", "fock_cycles",
+                                                 "fock_converged", "t_moments", "wall_s")},
+            "mixed": {k: it1["mixed"][k] for k in ("fock_cycles", "fock_converged", "t_moments",
+                                                   "wall_s")},
+            "note": "a Fock loop stopped at its cycle cap unconverged ends where its own "
+                    "dynamics take it: differences then measure that sensitivity, not the "
+                    "moment error"}
 
     if rank != 0:
         h.close()

@@ -133,7 +133,8 @@ int rot_limbs_slice4(const double* src, long long nrow, int ncol, long long ld, 
                      int ncolp, long long dst_rows, long long grp, long long gstride,
                      long long goff, __nv_bfloat16* dst, float* unit, cudaStream_t s);
 // W [nx][nQ][N] -> three-limb planes of the rows (x, p) over Q, rows
-// row0 + x N + p of [3][dst_rows][Qs], with certified units (stats: 3 nx N doubles).
+// row0 + x N + p of [3][dst_rows][Qs], with certified units (stats: nx N doubles
+// of scratch for the row units).
 int rot_transpose_slice3(const double* W, int nx, int nQ, int N, int Qs, double* stats,
                          long long dst_rows, long long row0, __nv_bfloat16* dst, float* unit,
                          cudaStream_t s);

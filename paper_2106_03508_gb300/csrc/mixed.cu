@@ -25,9 +25,10 @@
 // instruction.  GEMM 2 drains its tiles into the FP64 moments.
 //
 // Kernels: slice_rows_kernel (FP64 rotated rows -> limb planes),
-// gemm6_kernel<MODE_PAIR> (GEMM 1, writing X in FP32 for a block of pairs),
-// combine_kernel<0/1> (S/D and energy weights; exact per-row maxima of
-// Y w^n, then fixed-point limb planes of every Y w^n),
+// gemm6_kernel<MODE_PAIR> (GEMM 1, writing X in FP32 for a block of pairs; its
+// epilogue also takes the exact per-row maxima of every Y w^n),
+// combine_kernel (S/D and energy weights; fixed-point limb planes of every
+// Y w^n with the rows' units),
 // gemm6_kernel<MODE_MOMENT> (GEMM 2 for every moment, upper tiles, split-K,
 // FP64 atomics), mirror_tiles_kernel (the lower tiles).
 #include <cuda.h>
@@ -65,6 +66,53 @@ enum { MODE_PAIR = 0, MODE_MOMENT = 1 };
 // Device error codes (written to a device int).
 enum { DEV_OK = 0, DEV_TIMEOUT = 1 };
 
+constexpr int MAXM = 4;  // moments 0..3 on the split-precision path
+
+// a + b for unevaluated float pairs (hi, lo), renormalised (Knuth's TwoSum on
+// the high parts): about 2^-44 relative, so e_x + e_y - e_c rounds to FP32 as
+// the FP64 sum would (within an ulp) at FP32 rather than FP64 throughput.
+__device__ __forceinline__ float2 df_add(float2 a, float2 b) {
+  const float s = a.x + b.x;
+  const float bb = s - a.x;
+  const float e = (a.x - (s - bb)) + (b.x - bb);
+  const float t = e + (a.y + b.y);
+  const float hi = s + t;
+  return make_float2(hi, t - (hi - s));
+}
+
+// e[i] -> (hi, lo) float pair with hi + lo = e[i] to about 2^-48 relative.
+__global__ void float_pair_kernel(const double* __restrict__ e, int n, float2* __restrict__ out) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= n) return;
+  const float hi = (float)e[i];
+  out[i] = make_float2(hi, (float)(e[i] - (double)hi));
+}
+
+// Pair-symmetrised operand values for one (row, pair, inner pole): from
+// X_xy = a0 and X_yx = a1 (a1 = a0 on a diagonal pair x = y),
+//   Y_S = sqrt(cS) (a0 + a1), Y_D = sqrt(cD) (a0 - a1),
+// (cS, cD) = (1/2, 3/2) off the diagonal and (1/4, 0) on it, with sqrt(cS),
+// sqrt(cD) as unevaluated float pairs: a rounded FP32 constant would enter
+// U^(0) = Y Y^T squared and bias its diagonal (~7e-8).  The pair GEMM's
+// epilogue (row maxima) and the slicing pass call this same function on the
+// same FP32 inputs, so both see bit-identical Y.
+__device__ __forceinline__ void sd_values(float a0, float a1, bool diag, float& ys, float& yd) {
+  const float sS = diag ? 0.5f : 0.7071067690849304f;
+  const float sS_lo = diag ? 0.0f : 1.2101617485882343e-08f;
+  const float sD = diag ? 0.0f : 1.2247449159622192f;
+  const float sD_lo = diag ? 0.0f : -4.4570629853524224e-08f;
+  const float sum = a0 + a1, dif = a0 - a1;
+  ys = fmaf(sum, sS, sum * sS_lo);
+  yd = fmaf(dif, sD, dif * sD_lo);
+}
+
+// Energy weight e_x + e_y - e_c rounded to FP32, from float pairs
+// (ex = e_x + e_y already summed).
+__device__ __forceinline__ float pair_weight(float2 ex, float2 ec) {
+  const float2 w = df_add(ex, make_float2(-ec.x, -ec.y));
+  return w.x + w.y;
+}
+
 struct Params {
   int N;            // physical orbitals (rows of U)
   int n_in;         // inner pole count (c index)
@@ -79,11 +127,12 @@ struct Params {
   int nsplit;       // MODE_MOMENT: K splits per (tile, moment)
   int ntiles;       // tiles of this launch (the persistent CTAs loop over them)
   const int2* pairs;
-  const double* e_out;
-  const double* e_in;
+  const float2* e_out2;  // MODE_PAIR: pole energies as float pairs (outer, inner)
+  const float2* e_in2;
+  unsigned* maxbits;     // MODE_PAIR: [nm][N] row maxima of |Y w^n| (float bits)
   const float* unitA;   // MODE_PAIR: slicing unit of Lx rows [x][p]; MOMENT: [nm][N] of Y w^n rows
   const float* unitB;   // MODE_PAIR: unit of Lov rows [i][a];        MOMENT: of Y rows
-  int nm;               // MODE_MOMENT: moments computed (nmom + 1)
+  int nm;               // moments computed (nmom + 1)
   int v_stride;         // MODE_PAIR: v (row index of Lov rows is i * v + a)
   float* X;            // MODE_PAIR output: FP32 X_xy [N][np][2][ncp] (row stride Ks)
   int ncp;             // MODE_PAIR: n_cchunks * BN (padded inner count)
@@ -118,6 +167,30 @@ __device__ __forceinline__ void load_a(const CUtensorMap* mapA, uint8_t* dst, ui
     tc::tma_load_3d(dst, mapA, bar, ks * BK, s.a_row, s.a_plane * 3 + limb);
 }
 
+// L2 prefetch of everything one K stage of a segment loads (the producer runs
+// it PF_STAGES ahead of the loads).
+template <int MODE>
+__device__ __forceinline__ void prefetch_stage(const CUtensorMap* mapA, const CUtensorMap* mapB,
+                                               const Params& P, const Segment& s, int ks) {
+#pragma unroll
+  for (int l = 0; l < 3; ++l) {
+    if (MODE == MODE_PAIR) {
+      tc::tma_prefetch_3d(mapA, ks * BK, s.a_row, l * P.n_out + s.a_idx);
+      if (P.hole)
+        tc::tma_prefetch_4d(mapB, ks * BK, s.b_row, s.b_idx, l);
+      else
+        tc::tma_prefetch_4d(mapB, ks * BK, s.b_idx, s.b_row, l);
+    } else {
+      tc::tma_prefetch_3d(mapA, ks * BK, s.a_row, s.a_plane * 3 + l);
+      tc::tma_prefetch_3d(mapB, ks * BK, s.b_row, l);
+    }
+  }
+}
+
+// Stages between an L2 prefetch and the load of the same data (6 x 48 KB per
+// SM in flight, about a third of L2 over all SMs).
+constexpr int PF_STAGES = 6;
+
 // Work of one tile: one K segment into one accumulator set (nseg = 0: no
 // work, the tile is skipped by every role).
 struct TileWork {
@@ -134,12 +207,14 @@ __device__ __forceinline__ TileWork decode_tile(const Params& P, int t) {
   w.p0 = w.c0 = w.q0 = w.moment = w.pair_local = w.orient = 0;
   w.pr = make_int2(0, 0);
   if (MODE == MODE_PAIR) {
-    // ordered pair (x, y) (orient 0) or (y, x) (orient 1) of unordered pair x <= y
-    int b = t;
+    // ordered pair (x, y) (orient 0) or (y, x) (orient 1) of unordered pair
+    // x <= y; the two orientations of one (pair, p-tile, chunk) are
+    // consecutive tiles, taken by the same CTA (next_tile)
+    w.orient = t & 1;
+    int b = t >> 1;
     const int cc = b % P.n_cchunks; b /= P.n_cchunks;
     const int pt = b % P.n_ptiles; b /= P.n_ptiles;
-    w.orient = b & 1;
-    w.pair_local = b >> 1;
+    w.pair_local = b;
     w.pr = P.pairs[P.pair0 + w.pair_local];
     w.p0 = pt * BM;
     w.c0 = cc * BN;
@@ -147,9 +222,13 @@ __device__ __forceinline__ TileWork decode_tile(const Params& P, int t) {
     w.seg[0] = Segment{w.p0, xa, w.c0, yb, 0, 0, P.ksteps, 0};
     if (w.orient && w.pr.x == w.pr.y) w.nseg = 0;  // X_yx == X_xy on the diagonal
   } else {
-    // U is symmetric: only tiles with qt >= pt (upper triangle of tiles)
-    int b = t;
-    const int sp = b % P.nsplit; b /= P.nsplit;
+    // U is symmetric: only tiles with qt >= pt (upper triangle of tiles).
+    // Split-major order: the (tile, moment) items of one K split are
+    // neighbours, so the CTAs that read the same K range of the Y planes run
+    // together and share it through L2 instead of each fetching it from HBM.
+    const int ntm = P.n_ptiles * (P.n_ptiles + 1) / 2 * P.nm;
+    int b = t % ntm;
+    const int sp = t / ntm;
     w.moment = b % P.nm; b /= P.nm;
     int pt = 0, qt = 0;
     for (int r = 0, left = b; r < P.n_ptiles; ++r) {
@@ -166,7 +245,20 @@ __device__ __forceinline__ TileWork decode_tile(const Params& P, int t) {
   return w;
 }
 
-// Persistent kernel: CTA b handles tiles b, b + gridDim.x, ...
+// Tile order of the persistent CTAs.  MODE_PAIR: CTA b takes tiles 2s and
+// 2s + 1 (the two orientations of one pair tile) for s = b, b + grid, ..., so
+// its epilogue still holds X_xy when X_yx arrives; MODE_MOMENT: b, b + grid, ...
+template <int MODE>
+__device__ __forceinline__ int first_tile() {
+  return MODE == MODE_PAIR ? 2 * (int)blockIdx.x : (int)blockIdx.x;
+}
+template <int MODE>
+__device__ __forceinline__ int next_tile(int t) {
+  if (MODE == MODE_PAIR) return (t & 1) ? t + 2 * (int)gridDim.x - 1 : t + 1;
+  return t + (int)gridDim.x;
+}
+
+// Persistent kernel: CTA b handles the tiles of first_tile / next_tile
 //   warp 0: TMA producer (runs ahead across tiles through the smem ring)
 //   warp 1: TMEM allocation + single-thread tcgen05.mma issue
 //   warps 2..9: epilogue; warp w reads TMEM lane quarter w % 4 and column
@@ -223,9 +315,34 @@ gemm6_kernel(const __grid_constant__ CUtensorMap mapA, const __grid_constant__ C
     // ---------------- TMA producer ----------------
     tc::tma_prefetch(&mapA);
     tc::tma_prefetch(&mapB);
+    // L2 prefetch cursor, PF_STAGES stages ahead of the loads (across tiles)
+    int pf_tile = first_tile<MODE>(), pf_ks = 0;
+    TileWork pw;
+    bool pf_live = false;
+    auto pf_seek = [&]() {  // first stage of the next tile with work, from pf_tile on
+      pf_live = false;
+      for (; pf_tile < P.ntiles; pf_tile = next_tile<MODE>(pf_tile)) {
+        pw = decode_tile<MODE>(P, pf_tile);
+        if (pw.nseg > 0 && pw.seg[0].kbeg < pw.seg[0].kend) {
+          pf_ks = pw.seg[0].kbeg;
+          pf_live = true;
+          return;
+        }
+      }
+    };
+    auto pf_step = [&]() {
+      if (!pf_live) return;
+      prefetch_stage<MODE>(&mapA, &mapB, P, pw.seg[0], pf_ks);
+      if (++pf_ks >= pw.seg[0].kend) {
+        pf_tile = next_tile<MODE>(pf_tile);
+        pf_seek();
+      }
+    };
+    pf_seek();
+    for (int i = 0; i < PF_STAGES; ++i) pf_step();
     int t = 0;
     bool ok = true;
-    for (int tile = blockIdx.x; tile < P.ntiles && ok; tile += gridDim.x) {
+    for (int tile = first_tile<MODE>(); tile < P.ntiles && ok; tile = next_tile<MODE>(tile)) {
       const TileWork w = decode_tile<MODE>(P, tile);
       for (int si = 0; si < w.nseg && ok; ++si) {
         const Segment& s = w.seg[si];
@@ -251,6 +368,7 @@ gemm6_kernel(const __grid_constant__ CUtensorMap mapA, const __grid_constant__ C
             }
           }
           issued_sh = t + 1;
+          pf_step();
         }
       }
     }
@@ -262,7 +380,7 @@ gemm6_kernel(const __grid_constant__ CUtensorMap mapA, const __grid_constant__ C
     const int pb[5] = {0, 1, 2, 0, 1};
     int t = 0, lt = 0;
     bool ok = true;
-    for (int tile = blockIdx.x; tile < P.ntiles && ok; tile += gridDim.x) {
+    for (int tile = first_tile<MODE>(); tile < P.ntiles && ok; tile = next_tile<MODE>(tile)) {
       const TileWork w = decode_tile<MODE>(P, tile);
       if (w.nseg == 0) continue;
       const Segment& s = w.seg[0];
@@ -312,7 +430,7 @@ gemm6_kernel(const __grid_constant__ CUtensorMap mapA, const __grid_constant__ C
     const int col0 = half * (BN / 2);
     int lt = 0;
     bool ok = true;
-    for (int tile = blockIdx.x; tile < P.ntiles && ok; tile += gridDim.x) {
+    for (int tile = first_tile<MODE>(); tile < P.ntiles && ok; tile = next_tile<MODE>(tile)) {
       const TileWork w = decode_tile<MODE>(P, tile);
       if (w.nseg == 0) continue;
       const int p = w.p0 + r;
@@ -327,38 +445,80 @@ gemm6_kernel(const __grid_constant__ CUtensorMap mapA, const __grid_constant__ C
         const bool prow = p < P.N;
         const float uA = prow ? P.unitA[(long long)sg.a_idx * P.N + p] : 0.f;
         float* xrow = P.X + (long long)p * P.Ks +
-                      ((long long)w.pair_local * 2 + w.orient) * P.ncp + w.c0;
-        for (int cb = col0; cb < col0 + BN / 2; cb += 16) {
-          float hi[16], lo[16];
-          tc::tmem_ld16(trow + cb, hi);
-          tc::tmem_ld16(trow + BN + cb, lo);
+                      ((long long)w.pair_local * 2 + w.orient) * P.ncp + w.c0 + col0;
+        // with both orders of the pair tile at hand (orient 1, or orient 0 of a
+        // diagonal pair), the exact row maxima of |Y w^n| over this tile's
+        // columns, folded into the block's per-row maxima; X_xy comes back
+        // from this thread's own stores of the previous tile (same CTA)
+        const bool diag = w.pr.x == w.pr.y;
+        const bool take_max = prow && (w.orient == 1 || diag);
+        float2 ex = make_float2(0.f, 0.f);
+        if (take_max) ex = df_add(P.e_out2[w.pr.x], P.e_out2[w.pr.y]);
+        float mx[MAXM];
+#pragma unroll
+        for (int n = 0; n < MAXM; ++n) mx[n] = 0.f;
+#pragma unroll
+        for (int cb = 0; cb < BN / 2; cb += 16) {
+          float hi[16], lo[16], xv[16];
+          tc::tmem_ld16(trow + col0 + cb, hi);
+          tc::tmem_ld16(trow + BN + col0 + cb, lo);
+#pragma unroll
+          for (int c = 0; c < 16; ++c) {
+            const int ci = w.c0 + col0 + cb + c;
+            float x = 0.f;
+            if (prow && ci < P.n_in) {
+              // B-row units: hole rows (y, c) -> y*v + c ; particle rows (c, y) -> c*v + y
+              const long long rb = P.hole ? (long long)sg.b_idx * P.v_stride + ci
+                                          : (long long)ci * P.v_stride + sg.b_idx;
+              x = (hi[c] + lo[c]) * (uA * P.unitB[rb]);
+            }
+            xv[c] = x;
+          }
           if (prow) {
 #pragma unroll
-            for (int g = 0; g < 16; g += 4) {
-              float4 o4;
-              float* po = &o4.x;
+            for (int g = 0; g < 16; g += 4)
+              *reinterpret_cast<float4*>(xrow + cb + g) =
+                  make_float4(xv[g], xv[g + 1], xv[g + 2], xv[g + 3]);
+          }
+          if (take_max) {
+            float a0[16];  // X_xy
 #pragma unroll
-              for (int c = 0; c < 4; ++c) {
-                const int ci = w.c0 + cb + g + c;
-                float x = 0.f;
-                if (ci < P.n_in) {
-                  // B-row units: hole rows (y, c) -> y*v + c ; particle rows (c, y) -> c*v + y
-                  const long long rb = P.hole ? (long long)sg.b_idx * P.v_stride + ci
-                                              : (long long)ci * P.v_stride + sg.b_idx;
-                  x = (hi[g + c] + lo[g + c]) * (uA * P.unitB[rb]);
+            for (int g = 0; g < 16; g += 4) {
+              float4 t4 = diag ? make_float4(xv[g], xv[g + 1], xv[g + 2], xv[g + 3])
+                               : *reinterpret_cast<const float4*>(xrow - P.ncp + cb + g);
+              a0[g] = t4.x;
+              a0[g + 1] = t4.y;
+              a0[g + 2] = t4.z;
+              a0[g + 3] = t4.w;
+            }
+#pragma unroll
+            for (int c = 0; c < 16; ++c) {
+              const int ci = w.c0 + col0 + cb + c;
+              if (ci < P.n_in) {
+                float ys, yd;
+                sd_values(a0[c], xv[c], diag, ys, yd);
+                const float wt = pair_weight(ex, P.e_in2[ci]);
+#pragma unroll
+                for (int n = 0; n < MAXM; ++n) {
+                  if (n >= P.nm) break;
+                  mx[n] = fmaxf(mx[n], fmaxf(fabsf(ys), fabsf(yd)));
+                  ys *= wt;
+                  yd *= wt;
                 }
-                po[c] = x;
               }
-              *reinterpret_cast<float4*>(xrow + cb + g) = o4;
             }
           }
         }
-
         // this accumulator set may be overwritten once every epilogue warp is done
         tc::tc_fence_before();
         __syncwarp();
         if (lane == 0) tc::mbar_arrive(&acce_bar[buf]);
         ++lt;
+        if (take_max) {
+#pragma unroll
+          for (int n = 0; n < MAXM; ++n)
+            if (n < P.nm) atomicMax(P.maxbits + (long long)n * P.N + p, __float_as_uint(mx[n]));
+        }
       } else {
         // U^(n)[p][q] += u(p) u(q) sum over the tile's chunks of (hi + lo):
         // chunks summed in FP32 registers, one FP64 atomic per element
@@ -388,11 +548,14 @@ gemm6_kernel(const __grid_constant__ CUtensorMap mapA, const __grid_constant__ C
         if (!ok) break;
         if (p < P.N) {
           double* U = P.U0 + (long long)w.moment * P.N * P.N + (long long)p * P.N;
-          const double uA = (double)P.unitA[(long long)w.moment * P.N + p];
+          // acc u(p) u(q) with power-of-two units: an exponent shift, formed
+          // on the integer pipe (scale_to_double), then the FP64 atomic
+          const int kA = tc::pow2_exp(P.unitA[(long long)w.moment * P.N + p]);
 #pragma unroll
           for (int c = 0; c < BN / 2; ++c) {
             const int q = w.q0 + col0 + c;
-            if (q < P.N) atomicAdd(U + q, (double)acc[c] * (uA * (double)P.unitB[q]));
+            if (q < P.N && acc[c] != 0.f)
+              atomicAdd(U + q, tc::scale_to_double(acc[c], kA + tc::pow2_exp(P.unitB[q])));
           }
         }
       }
@@ -443,26 +606,29 @@ __global__ void slice_rows_kernel(const T* __restrict__ src, long long nrow, int
        r += nwarps) {
     const T* row = src + r * ld;
     const long long dr = (r / grp) * gstride + goff + r % grp;
-    double m = 0.0, s2 = 0.0, s1 = 0.0;
-    for (int c = lane; c < ncol; c += 32) {
-      const double x = fabs((double)row[c]);
-      m = fmax(m, x);
-      s2 = fma(x, x, s2);
-      s1 += x;
-    }
+    tc::RowStats st;  // integer and FP32 pipes only
+    for (int c = lane; c < ncol; c += 32) st.add((double)row[c]);
+    st.warp_reduce();
+    double u;
+    if (!st.unit((double)ncolp, u)) {  // a bound overflowed the float range: FP64 sums
+      double s2 = 0.0, s1 = 0.0;
+      for (int c = lane; c < ncol; c += 32) {
+        const double x = fabs((double)row[c]);
+        s2 = fma(x, x, s2);
+        s1 += x;
+      }
 #pragma unroll
-    for (int o = 16; o > 0; o >>= 1) {
-      m = fmax(m, __shfl_xor_sync(0xffffffffu, m, o));
-      s2 += __shfl_xor_sync(0xffffffffu, s2, o);
-      s1 += __shfl_xor_sync(0xffffffffu, s1, o);
+      for (int o = 16; o > 0; o >>= 1) {
+        s2 += __shfl_xor_sync(0xffffffffu, s2, o);
+        s1 += __shfl_xor_sync(0xffffffffu, s1, o);
+      }
+      u = tc::certified_unit(__longlong_as_double((long long)st.mb), s2, s1, (double)ncolp);
     }
-    const double u = tc::certified_unit(m, s2, s1, (double)ncolp);
-    const double inv = 1.0 / u;  // exact: u is a power of two
+    const int ku = tc::pow2_exp(u);
     __nv_bfloat16* d = dst + dr * ncolp;
     for (int c = lane; c < ncolp; c += 32) {
-      const double x = (c < ncol) ? (double)row[c] : 0.0;
       __nv_bfloat16 h0, h1, h2;
-      tc::slice3(x * inv, h0, h1, h2);
+      tc::slice3_int((c < ncol) ? (double)row[c] : 0.0, ku, h0, h1, h2);
       d[c] = h0;
       d[plane + c] = h1;
       d[2 * plane + c] = h2;
@@ -471,27 +637,22 @@ __global__ void slice_rows_kernel(const T* __restrict__ src, long long nrow, int
   }
 }
 
-// Pair-symmetrised operands of GEMM 2 from the pair GEMM's X (Eqs.
-// mp2_zeroth_moment / mp2_first_moment in S/D form): for unordered pair
-// (x, y), inner pole c and row p,
-//   S = X_xy + X_yx, D = X_xy - X_yx, Y_S = sqrt(cS) S, Y_D = sqrt(cD) D,
-//   Yw = (e_x + e_y - e_c) Y.
-// PASS 0 takes each row's exact max |Y| and |Yw| over the block (atomicMax on
-// the float bits of non-negative values); PASS 1 slices Y and Yw in fixed
-// point with those units into the limb planes at K index
-// pair * kpp + chunk * 256 + (S: c, D: 128 + c).  Exact maxima matter: a unit
-// from a bound (e.g. sqrt(6) max|X|) coarsens the grid and the squared
-// rounding error biases diag U^(0) (measured +1e-8 relative).  Four
+// Slicing pass of GEMM 2's operands (Eqs. mp2_zeroth_moment /
+// mp2_first_moment in S/D form): for unordered pair (x, y), inner pole c and
+// row p, Y_S, Y_D from X_xy, X_yx (sd_values) and Yw^n = (e_x + e_y - e_c)^n Y,
+// sliced in fixed point with each row's unit from the exact row maxima that
+// the pair GEMM's epilogue took over the whole block, into the limb planes at
+// K index pair * kpp + chunk * 256 + (S: c, D: 128 + c).  Exact maxima
+// matter: a unit from a bound (e.g. sqrt(6) max|X|) coarsens the grid and the
+// squared rounding error biases diag U^(0) (measured +1e-8 relative).  Four
 // consecutive c per thread; grid = (blocks over pair x inner / 4, N rows).
-constexpr int MAXM = 4;  // moments 0..3 on the split-precision path
-
 struct Combine {
   const float* X;
   long long xrow;  // row stride of X
   int np, ncp, n_in, N, kpp, pair0, nm;
   const int2* pairs;
-  const double* e_out;
-  const double* e_in;
+  const float2* e_out;  // pole energies as unevaluated float pairs (hi, lo)
+  const float2* e_in;
   unsigned* maxbits;   // [nm][N]: max |Y w^n| per row
   __nv_bfloat16* Y;    // [nm][3][N][Ks] limb planes of Y w^n
   long long Ks, plane; // plane = N Ks
@@ -511,19 +672,16 @@ __device__ __forceinline__ void store4(__nv_bfloat16* base, long long plane, lon
   }
 }
 
-template <int PASS>
 __global__ void __launch_bounds__(256) combine_kernel(const Combine C) {
   const int p = blockIdx.y;
   const int nq = C.ncp / 4;  // groups of 4 inner poles per pair
   const int total = C.np * nq;
-  float iu[MAXM], mx[MAXM];
+  float iu[MAXM];
 #pragma unroll
-  for (int n = 0; n < MAXM; ++n) {
-    iu[n] = 1.f;
-    mx[n] = 0.f;
-    if (PASS == 1 && n < C.nm)
-      iu[n] = 1.0f / tc::slice_unitf(__uint_as_float(C.maxbits[(long long)n * C.N + p]), 8);
-  }
+  for (int n = 0; n < MAXM; ++n)
+    iu[n] = n < C.nm
+                ? 1.0f / tc::slice_unitf(__uint_as_float(C.maxbits[(long long)n * C.N + p]), 8)
+                : 1.f;
   const float* xr = C.X + (long long)p * C.xrow;
   for (int e = blockIdx.x * blockDim.x + threadIdx.x; e < total; e += gridDim.x * blockDim.x) {
     const int pl = e / nq, c0 = (e - pl * nq) * 4;
@@ -531,13 +689,7 @@ __global__ void __launch_bounds__(256) combine_kernel(const Combine C) {
     const bool diag = pr.x == pr.y;
     const float4 x0 = *reinterpret_cast<const float4*>(xr + (2LL * pl) * C.ncp + c0);
     const float4 x1 = diag ? x0 : *reinterpret_cast<const float4*>(xr + (2LL * pl + 1) * C.ncp + c0);
-    // sqrt(cS), sqrt(cD) as unevaluated float pairs: a rounded FP32 constant
-    // would enter U^(0) = Y Y^T squared and bias its diagonal (~7e-8)
-    const float sS = diag ? 0.5f : 0.7071067690849304f;
-    const float sS_lo = diag ? 0.0f : 1.2101617485882343e-08f;
-    const float sD = diag ? 0.0f : 1.2247449159622192f;
-    const float sD_lo = diag ? 0.0f : -4.4570629853524224e-08f;
-    const double ex = C.e_out[pr.x] + C.e_out[pr.y];
+    const float2 ex = df_add(C.e_out[pr.x], C.e_out[pr.y]);
     const float a0[4] = {x0.x, x0.y, x0.z, x0.w};
     const float a1[4] = {x1.x, x1.y, x1.z, x1.w};
     float ys[4], yd[4], wt[4];
@@ -546,30 +698,23 @@ __global__ void __launch_bounds__(256) combine_kernel(const Combine C) {
       const int c = c0 + j;
       ys[j] = yd[j] = wt[j] = 0.f;
       if (c < C.n_in) {
-        const float sum = a0[j] + a1[j], dif = a0[j] - a1[j];
-        ys[j] = fmaf(sum, sS, sum * sS_lo);
-        yd[j] = fmaf(dif, sD, dif * sD_lo);
-        wt[j] = (float)(ex - C.e_in[c]);
+        sd_values(a0[j], a1[j], diag, ys[j], yd[j]);
+        wt[j] = pair_weight(ex, C.e_in[c]);
       }
     }
     const long long k = (long long)pl * C.kpp + (c0 / BN) * KCHUNK + (c0 % BN);
 #pragma unroll
     for (int n = 0; n < MAXM; ++n) {
       if (n >= C.nm) break;
-      if (PASS == 0) {
+      __nv_bfloat16 hs[3][4], hd[3][4];
 #pragma unroll
-        for (int j = 0; j < 4; ++j) mx[n] = fmaxf(mx[n], fmaxf(fabsf(ys[j]), fabsf(yd[j])));
-      } else {
-        __nv_bfloat16 hs[3][4], hd[3][4];
-#pragma unroll
-        for (int j = 0; j < 4; ++j) {
-          tc::slice3f(ys[j] * iu[n], hs[0][j], hs[1][j], hs[2][j]);
-          tc::slice3f(yd[j] * iu[n], hd[0][j], hd[1][j], hd[2][j]);
-        }
-        __nv_bfloat16* base = C.Y + (long long)n * 3 * C.plane + (long long)p * C.Ks;
-        store4(base, C.plane, k, hs);
-        store4(base, C.plane, k + BN, hd);
+      for (int j = 0; j < 4; ++j) {
+        tc::slice3f(ys[j] * iu[n], hs[0][j], hs[1][j], hs[2][j]);
+        tc::slice3f(yd[j] * iu[n], hd[0][j], hd[1][j], hd[2][j]);
       }
+      __nv_bfloat16* base = C.Y + (long long)n * 3 * C.plane + (long long)p * C.Ks;
+      store4(base, C.plane, k, hs);
+      store4(base, C.plane, k + BN, hd);
       // next power: Y w^(n+1)
 #pragma unroll
       for (int j = 0; j < 4; ++j) {
@@ -578,25 +723,9 @@ __global__ void __launch_bounds__(256) combine_kernel(const Combine C) {
       }
     }
   }
-  if (PASS == 0) {
-    __shared__ float sh[MAXM][8];
-#pragma unroll
-    for (int n = 0; n < MAXM; ++n) {
-      float m = mx[n];
-#pragma unroll
-      for (int o = 16; o > 0; o >>= 1) m = fmaxf(m, __shfl_xor_sync(0xffffffffu, m, o));
-      if ((threadIdx.x & 31) == 0) sh[n][threadIdx.x >> 5] = m;
-    }
-    __syncthreads();
-    if (threadIdx.x < C.nm) {
-      float m = 0.f;
-      for (int w = 0; w < (int)(blockDim.x >> 5); ++w) m = fmaxf(m, sh[threadIdx.x][w]);
-      atomicMax(C.maxbits + (long long)threadIdx.x * C.N + p, __float_as_uint(m));
-    }
-  } else if (blockIdx.x == 0 && threadIdx.x < C.nm) {
+  if (blockIdx.x == 0 && threadIdx.x < C.nm)
     C.unit[(long long)threadIdx.x * C.N + p] =
         tc::slice_unitf(__uint_as_float(C.maxbits[(long long)threadIdx.x * C.N + p]), 8);
-  }
 }
 
 // Lower off-diagonal tiles of U (never computed) <- their upper mirror.
@@ -653,7 +782,10 @@ struct Buffers {
 struct MixedWs {
   Buffers lx_o, lx_v, l_ov, y, pairs, err;
   Buffers u_xo, u_xv, u_ov, u_y, x32, maxbits, rot;
-  Buffers l4, u_l4, co4, cv4, u_co, u_cv, rot_stats, w4, u_w4, rot_ov;
+  Buffers l4, u_l4, co4, cv4, u_co, u_cv, rot_stats, w4, u_w4, rot_ov, e2;
+  Buffers y2, x32b, maxbits2, u_y2;  // second set of pair-block buffers
+  cudaStream_t side = nullptr;       // slicing passes, overlapping the next pair GEMM
+  cudaEvent_t ev_pair[2] = {nullptr, nullptr}, ev_comb[2] = {nullptr, nullptr};
 };
 
 std::mutex g_attr_mu;
@@ -686,10 +818,25 @@ void mixed_workspace_destroy(void* w) {
   MixedWs* W = static_cast<MixedWs*>(w);
   for (Buffers* b : {&W->lx_o, &W->lx_v, &W->l_ov, &W->y, &W->pairs, &W->err, &W->u_xo,
                      &W->u_xv, &W->u_ov, &W->u_y, &W->x32, &W->maxbits, &W->rot, &W->l4, &W->u_l4, &W->co4,
-                     &W->cv4, &W->u_co, &W->u_cv, &W->rot_stats, &W->w4, &W->u_w4, &W->rot_ov})
+                     &W->cv4, &W->u_co, &W->u_cv, &W->rot_stats, &W->w4, &W->u_w4, &W->rot_ov,
+                     &W->e2, &W->y2, &W->x32b, &W->maxbits2, &W->u_y2})
     if (b->p) cudaFree(b->p);
+  for (int i = 0; i < 2; ++i) {
+    if (W->ev_pair[i]) cudaEventDestroy(W->ev_pair[i]);
+    if (W->ev_comb[i]) cudaEventDestroy(W->ev_comb[i]);
+  }
+  if (W->side) cudaStreamDestroy(W->side);
   delete W;
 }
+
+#define CK_SIDE(call)                                                          \
+  do {                                                                         \
+    const cudaError_t e_ = (call);                                             \
+    if (e_ != cudaSuccess) {                                                   \
+      err = std::string(#call ": ") + cudaGetErrorString(e_);                  \
+      return AGF2_ERR_CUDA;                                                    \
+    }                                                                          \
+  } while (0)
 
 int mixed_build_moments(const double* L, int naux, int N, const double* Co, const double* Cv,
                         int o, int v, const double* eo, const double* ev, int nmom,
@@ -786,7 +933,7 @@ int mixed_build_moments(const double* L, int naux, int N, const double* Co, cons
     const int bi = (int)std::max<long long>(1, std::min<long long>(o, budget / per_o));
     const int ba = (int)std::max<long long>(1, std::min<long long>(v, budget / per_v));
     double* wtmp = grow<double>(W.rot, (size_t)std::max<long long>((long long)bi, ba) * nQN, err);
-    double* stats = grow<double>(W.rot_stats, 3 * (size_t)std::max(bi, ba) * N, err);
+    double* stats = grow<double>(W.rot_stats, (size_t)std::max(bi, ba) * N, err);
     __nv_bfloat16* w4 = grow<__nv_bfloat16>(W.w4, 4LL * ba * naux * Ns, err);
     float* u_w4 = grow<float>(W.u_w4, (size_t)ba * naux, err);
     double* tmpov = grow<double>(W.rot_ov, (size_t)o * ba * naux, err);
@@ -844,13 +991,36 @@ int mixed_build_moments(const double* L, int naux, int N, const double* Co, cons
   }
 
   const int n_ptiles = (N + BM - 1) / BM;
+  // pole energies as float pairs for the combine pass's weights: [eo | ev]
+  float2* e2 = grow<float2>(W.e2, (size_t)o + v, err);
+  if (!e2) return AGF2_ERR_OOM;
+  if (o > 0) float_pair_kernel<<<(o + 255) / 256, 256, 0, s>>>(eo, o, e2);
+  if (v > 0) float_pair_kernel<<<(v + 255) / 256, 256, 0, s>>>(ev, v, e2 + o);
+  count_launch((o > 0) + (v > 0));
+  // the slicing pass of pair block b runs on a side stream while the pair GEMM
+  // of block b + 1 runs on s (two sets of block buffers); every side-stream
+  // launch is joined back into s by an event before the block's moment GEMM
+  if (!W.side) {
+    if (cudaStreamCreateWithFlags(&W.side, cudaStreamNonBlocking) != cudaSuccess) {
+      err = "side stream creation failed";
+      return AGF2_ERR_CUDA;
+    }
+    for (int i = 0; i < 2; ++i)
+      if (cudaEventCreateWithFlags(&W.ev_pair[i], cudaEventDisableTiming) != cudaSuccess ||
+          cudaEventCreateWithFlags(&W.ev_comb[i], cudaEventDisableTiming) != cudaSuccess) {
+        err = "event creation failed";
+        return AGF2_ERR_CUDA;
+      }
+  }
+  float* u_yb[2] = {u_y, grow<float>(W.u_y2, (size_t)nm * N, err)};
+  if (!u_yb[1]) return AGF2_ERR_OOM;
   for (int sector = 0; sector < 2; ++sector) {
     const bool hole = (sector == 0);
     const int n_out = hole ? o : v;
     const int n_in = hole ? v : o;
-    const double* e_out = hole ? eo : ev;
-    const double* e_in = hole ? ev : eo;
     double* U = hole ? U_hole : U_part;
+    const float2* e_out2 = hole ? e2 : e2 + o;
+    const float2* e_in2 = hole ? e2 + o : e2;
     // unordered pairs x <= y
     std::vector<int2> pairs;
     pairs.reserve((size_t)n_out * (n_out + 1) / 2);
@@ -872,8 +1042,8 @@ int mixed_build_moments(const double* L, int naux, int N, const double* Co, cons
     const int tpp = 2 * n_ptiles * n_cchunks;  // tiles per unordered pair
     int bp = (int)std::max(1.0, std::floor(1.0e9 / per_pair));
     {
-      int g = nsm, t = tpp;
-      while (t) { const int r = g % t; g = t; t = r; }  // gcd(nsm, tpp)
+      int g = nsm, t = tpp / 2;  // a CTA takes both orientations of a pair tile
+      while (t) { const int r = g % t; g = t; t = r; }  // gcd(nsm, tpp / 2)
       const int unit = nsm / g;                          // pairs per whole wave
       const int bp_lim = (int)std::floor(1.5e9 / per_pair);
       if (unit <= bp_lim) bp = std::max(unit, bp / unit * unit);
@@ -881,53 +1051,23 @@ int mixed_build_moments(const double* L, int naux, int N, const double* Co, cons
     bp = std::max(1, std::min<int>(bp, (int)pairs.size()));
     const long long Ks = (long long)bp * kpp;
     const long long Kx = (long long)bp * 2 * ncp;  // row length of X
-    __nv_bfloat16* y = grow<__nv_bfloat16>(W.y, 3LL * nm * N * Ks, err);  // [nm][3][N][Ks]
-    float* x32 = grow<float>(W.x32, (size_t)N * Kx, err);
-    unsigned* maxbits = grow<unsigned>(W.maxbits, (size_t)nm * N, err);
-    if (!y || !x32 || !maxbits) return AGF2_ERR_OOM;
-    for (size_t b0 = 0; b0 < pairs.size(); b0 += bp) {
-      const int np = (int)std::min<size_t>(bp, pairs.size() - b0);
-      const long long K = (long long)np * kpp;
-      Params P{};
-      P.N = N;
-      P.n_in = n_in;
-      P.ksteps = Qs / BK;
-      P.n_ptiles = n_ptiles;
-      P.n_cchunks = n_cchunks;
-      P.n_out = n_out;
-      P.hole = hole ? 1 : 0;
-      P.pair0 = (int)b0;
-      P.pairs = dpairs;
-      P.e_out = e_out;
-      P.e_in = e_in;
-      P.unitA = hole ? u_xo : u_xv;
-      P.unitB = u_ov;
-      P.v_stride = v;
-      P.X = x32;
-      P.ncp = ncp;
-      P.Ks = Kx;
-      P.err = derr;
-      P.ntiles = np * tpp;
-
-      const int grid1 = std::min(P.ntiles, nsm);
-      // algorithmic flops: GEMM 1 for the ordered pairs of this block
+    __nv_bfloat16* yb[2] = {grow<__nv_bfloat16>(W.y, 3LL * nm * N * Ks, err),  // [nm][3][N][Ks]
+                            grow<__nv_bfloat16>(W.y2, 3LL * nm * N * Ks, err)};
+    float* xb[2] = {grow<float>(W.x32, (size_t)N * Kx, err), grow<float>(W.x32b, (size_t)N * Kx, err)};
+    unsigned* mb[2] = {grow<unsigned>(W.maxbits, (size_t)nm * N, err),
+                       grow<unsigned>(W.maxbits2, (size_t)nm * N, err)};
+    if (!yb[0] || !yb[1] || !xb[0] || !xb[1] || !mb[0] || !mb[1]) return AGF2_ERR_OOM;
+    // block whose moment GEMM is launched after the next block's pair GEMM
+    struct Pending {
+      bool valid = false;
+      int buf = 0;
+      long long K = 0;
       long long ordered = 0;
-      for (int t = 0; t < np; ++t) ordered += (pairs[b0 + t].x == pairs[b0 + t].y) ? 1 : 2;
-      mark(0, 2.0 * N * (double)naux * n_in * (double)ordered);
-      gemm6_kernel<MODE_PAIR><<<grid1, NTHREADS, SMEM_BYTES, s>>>(
-          hole ? map_xo : map_xv, hole ? map_b_hole : map_b_part, P);
-      mark_end();
-      count_launch();
-      // S/D and energy weights, then fixed-point limbs with each row's exact unit
-      Combine C{x32, Kx, np, ncp, n_in, N, (int)kpp, (int)b0, nm, dpairs, e_out, e_in, maxbits,
-                y, Ks, (long long)N * Ks, u_y};
-      cudaMemsetAsync(maxbits, 0, (size_t)nm * N * sizeof(unsigned), s);
-      const long long per_row = (long long)np * ncp / 4;
-      const dim3 gc((unsigned)std::max(1LL, std::min<long long>((per_row + 1023) / 1024, 64)),
-                    (unsigned)N);
-      combine_kernel<0><<<gc, 256, 0, s>>>(C);
-      combine_kernel<1><<<gc, 256, 0, s>>>(C);
-      count_launch(2);
+    } pend;
+    auto launch_moment = [&](const Pending& pb) -> int {
+      CK_SIDE(cudaStreamWaitEvent(s, W.ev_comb[pb.buf], 0));
+      __nv_bfloat16* y = yb[pb.buf];
+      const long long K = pb.K;
       // GEMM 2 over this block's K = np * kpp
       CUtensorMap map_y;  // all [nm][3] planes; plane index = moment * 3 + limb
       cuuint64_t dims[3] = {(cuuint64_t)K, (cuuint64_t)N, (cuuint64_t)3 * nm};
@@ -951,21 +1091,88 @@ int mixed_build_moments(const double* L, int naux, int N, const double* Co, cons
       M.nsplit = (M.ksteps + M.ksplit - 1) / M.ksplit;  // every split non-empty
       M.ntiles = tiles * M.nsplit;
       M.n_out = 0;
-      M.unitA = u_y;
-      M.unitB = u_y;
+      M.unitA = u_yb[pb.buf];
+      M.unitB = u_yb[pb.buf];
       M.U0 = U;
       M.err = derr;
       // algorithmic flops: every moment over the ordered pairs, 2 N^2 per (pair, c)
-      mark(1, 2.0 * nm * (double)N * N * (double)n_in * (double)ordered);
-      gemm6_kernel<MODE_MOMENT><<<std::min(M.ntiles, nsm), NTHREADS, SMEM_BYTES, s>>>(map_y, map_y,
-                                                                                      M);
+      mark(1, 2.0 * nm * (double)N * N * (double)n_in * (double)pb.ordered);
+      gemm6_kernel<MODE_MOMENT><<<std::min(M.ntiles, nsm), NTHREADS, SMEM_BYTES, s>>>(map_y,
+                                                                                      map_y, M);
       mark_end();
       count_launch();
-      cudaError_t e = cudaGetLastError();
+      const cudaError_t e = cudaGetLastError();
       if (e != cudaSuccess) {
         err = std::string("tcgen05 kernel launch: ") + cudaGetErrorString(e);
         return AGF2_ERR_CUDA;
       }
+      return AGF2_OK;
+    };
+    int bi = 0;
+    for (size_t b0 = 0; b0 < pairs.size(); b0 += bp, ++bi) {
+      const int cur = bi & 1;
+      const int np = (int)std::min<size_t>(bp, pairs.size() - b0);
+      const long long K = (long long)np * kpp;
+      float* x32 = xb[cur];
+      unsigned* maxbits = mb[cur];
+      Params P{};
+      P.N = N;
+      P.n_in = n_in;
+      P.ksteps = Qs / BK;
+      P.n_ptiles = n_ptiles;
+      P.n_cchunks = n_cchunks;
+      P.n_out = n_out;
+      P.hole = hole ? 1 : 0;
+      P.pair0 = (int)b0;
+      P.pairs = dpairs;
+      P.e_out2 = e_out2;
+      P.e_in2 = e_in2;
+      P.maxbits = maxbits;
+      P.nm = nm;
+      P.unitA = hole ? u_xo : u_xv;
+      P.unitB = u_ov;
+      P.v_stride = v;
+      P.X = x32;
+      P.ncp = ncp;
+      P.Ks = Kx;
+      P.err = derr;
+      P.ntiles = np * tpp;
+
+      const int grid1 = std::min(P.ntiles / 2, nsm);  // tpp is even: whole orientation pairs
+      // algorithmic flops: GEMM 1 for the ordered pairs of this block
+      long long ordered = 0;
+      for (int t = 0; t < np; ++t) ordered += (pairs[b0 + t].x == pairs[b0 + t].y) ? 1 : 2;
+      mark(0, 2.0 * N * (double)naux * n_in * (double)ordered);
+      // the epilogue folds each pair tile's row maxima of |Y w^n| into maxbits
+      cudaMemsetAsync(maxbits, 0, (size_t)nm * N * sizeof(unsigned), s);
+      gemm6_kernel<MODE_PAIR><<<grid1, NTHREADS, SMEM_BYTES, s>>>(
+          hole ? map_xo : map_xv, hole ? map_b_hole : map_b_part, P);
+      mark_end();
+      count_launch();
+      CK_SIDE(cudaEventRecord(W.ev_pair[cur], s));
+      // S/D and energy weights, then fixed-point limbs with each row's exact
+      // unit, on the side stream (overlaps the next block's pair GEMM)
+      CK_SIDE(cudaStreamWaitEvent(W.side, W.ev_pair[cur], 0));
+      Combine C{x32, Kx, np, ncp, n_in, N, (int)kpp, (int)b0, nm, dpairs, e_out2, e_in2, maxbits,
+                yb[cur], Ks, (long long)N * Ks, u_yb[cur]};
+      const long long per_row = (long long)np * ncp / 4;
+      const dim3 gc((unsigned)std::max(1LL, std::min<long long>((per_row + 1023) / 1024, 64)),
+                    (unsigned)N);
+      combine_kernel<<<gc, 256, 0, W.side>>>(C);
+      count_launch();
+      CK_SIDE(cudaEventRecord(W.ev_comb[cur], W.side));
+      if (pend.valid) {
+        const int rc = launch_moment(pend);
+        if (rc != AGF2_OK) return rc;
+      }
+      pend.valid = true;
+      pend.buf = cur;
+      pend.K = K;
+      pend.ordered = ordered;
+    }
+    if (pend.valid) {
+      const int rc = launch_moment(pend);
+      if (rc != AGF2_OK) return rc;
     }
   }
   {

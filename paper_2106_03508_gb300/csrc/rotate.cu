@@ -241,13 +241,18 @@ rot4_kernel(const __grid_constant__ CUtensorMap mapA, const __grid_constant__ CU
       if (!ok) break;
       const int m = m0 + r;
       if (m < P.M) {
-        const double ua = (double)P.unitA[P.a_row0 + m];
+        // (ah + al) u_a u_b: the power-of-two units as exponent shifts on the
+        // integer pipe, one FP64 add per element
+        const int ka = tc::pow2_exp(P.unitA[P.a_row0 + m]);
         const float* ub = P.unitB + (long long)b * P.Nn;
         double* o = P.out + (long long)m * P.sOm + (long long)b * P.sOb;
 #pragma unroll
         for (int c = 0; c < R_EPI_COLS; ++c) {
           const int n = n0 + col0 + c;
-          if (n < P.Nn) o[n] = ((double)ah[c] + (double)al[c]) * (ua * (double)ub[n]);
+          if (n < P.Nn) {
+            const int k = ka + tc::pow2_exp(ub[n]);
+            o[n] = tc::scale_to_double(ah[c], k) + tc::scale_to_double(al[c], k);
+          }
         }
       }
     }
@@ -294,58 +299,71 @@ __global__ void slice4_rows_kernel(const double* __restrict__ src, long long nro
        r += nwarps) {
     const double* row = src + r * ld;
     const long long dr = (r / grp) * gstride + goff + r % grp;
-    double m = 0.0;
-    for (int c = lane; c < ncol; c += 32) m = fmax(m, fabs(row[c * cs]));
+    unsigned long long mb = 0;  // max |x| on the integer pipe
+    for (int c = lane; c < ncol; c += 32) mb = max(mb, tc::abs_bits(row[c * cs]));
 #pragma unroll
-    for (int o = 16; o > 0; o >>= 1) m = fmax(m, __shfl_xor_sync(0xffffffffu, m, o));
-    const double u = tc::slice_unit(m, 7);
-    const double inv = 1.0 / u;  // exact: a power of two
+    for (int o = 16; o > 0; o >>= 1)
+      mb = max(mb, (unsigned long long)__shfl_xor_sync(0xffffffffu, (long long)mb, o));
+    const double u = tc::slice_unit(__longlong_as_double((long long)mb), 7);
+    const int ku = tc::pow2_exp(u);
     __nv_bfloat16* d = dst + dr * ncolp;
     for (int c = lane; c < ncolp; c += 32) {
-      double v = (c < ncol) ? row[c * cs] * inv : 0.0;
+      // integer digits of x / u (integer pipe): |d0| <= 128, |d_l| <= 128
+      int dg[RNL];
+      tc::fixed_digits<RNL>((c < ncol) ? row[c * cs] : 0.0, ku, dg);
 #pragma unroll
-      for (int l = 0; l < RNL; ++l) {
-        const double a = rint(v);
-        d[l * plane + c] = __double2bfloat16(a);
-        v = (v - a) * 256.0;
-      }
+      for (int l = 0; l < RNL; ++l) d[l * plane + c] = __float2bfloat16_rn((float)dg[l]);
     }
     if (lane == 0) unit[dr] = (float)u;
   }
 }
 
-// Per (x, p): max |W[x][Q][p]| and the sums of W^2 and |W| over Q, for the
-// unit and exactness certificate of the rows (x, p) over Q.  Thread per p
-// (coalesced over p), grid (ceil(N / 256), nx).
-__global__ void col_stats_kernel(const double* __restrict__ W, int nQ, int N,
-                                 double* __restrict__ stats) {
-  const int p = blockIdx.x * blockDim.x + threadIdx.x;
+// Per (x, p): the certified unit (tc::certified_unit) of the row (x, p) over
+// Q, from tc::RowStats (integer and FP32 pipes).  Block of 32 p x 8 Q-groups
+// (coalesced over p), grid (ceil(N / 32), nx).
+__global__ void col_stats_kernel(const double* __restrict__ W, int nQ, int N, int Qs,
+                                 double* __restrict__ unit_out) {
+  __shared__ unsigned long long smb[8][32];
+  __shared__ float ss2[8][32], ss1[8][32];
+  const int tx = threadIdx.x & 31, ty = threadIdx.x >> 5;
+  const int p = blockIdx.x * 32 + tx;
   const int x = blockIdx.y;
-  if (p >= N) return;
-  const double* w = W + (long long)x * nQ * N + p;
-  double m = 0.0, s2 = 0.0, s1 = 0.0;
-  for (int Q = 0; Q < nQ; ++Q) {
-    const double v = fabs(w[(long long)Q * N]);
-    m = fmax(m, v);
-    s2 = fma(v, v, s2);
-    s1 += v;
+  tc::RowStats st;
+  if (p < N) {
+    const double* w = W + (long long)x * nQ * N + p;
+    for (int Q = ty; Q < nQ; Q += 8) st.add(w[(long long)Q * N]);
   }
-  double* o = stats + 3 * ((long long)x * N + p);
-  o[0] = m;
-  o[1] = s2;
-  o[2] = s1;
+  smb[ty][tx] = st.mb;
+  ss2[ty][tx] = st.s2;
+  ss1[ty][tx] = st.s1;
+  __syncthreads();
+  if (ty != 0 || p >= N) return;
+  for (int g = 1; g < 8; ++g) st.merge(smb[g][tx], ss2[g][tx], ss1[g][tx]);
+  double u;
+  if (!st.unit((double)Qs, u)) {  // a bound overflowed the float range: FP64 sums
+    const double* w = W + (long long)x * nQ * N + p;
+    double s2 = 0.0, s1 = 0.0;
+    for (int Q = 0; Q < nQ; ++Q) {
+      const double v = fabs(w[(long long)Q * N]);
+      s2 = fma(v, v, s2);
+      s1 += v;
+    }
+    u = tc::certified_unit(__longlong_as_double((long long)st.mb), s2, s1, (double)Qs);
+  }
+  unit_out[(long long)x * N + p] = u;
 }
 
 // W[x][Q][p] -> three BF16 limb planes of the rows (x, p) over Q (rows
-// x0 N + x N + p of planes [3][dst_rows][Qs]) with the certified unit of
-// tc::certified_unit (every h0 h0' partial sum of the pair GEMM exact).
+// x0 N + x N + p of planes [3][dst_rows][Qs]) with the row units of
+// col_stats_kernel (every h0 h0' partial sum of the pair GEMM exact).
 // Block (32 x 8 threads) per (x, 32 p, 32 Q) tile, transposed through
 // shared memory so both the reads (over p) and the writes (over Q) coalesce.
 __global__ void transpose_slice3_kernel(const double* __restrict__ W, int nQ, int N, int Qs,
-                                        const double* __restrict__ stats, long long dst_rows,
+                                        const double* __restrict__ unit_in, long long dst_rows,
                                         long long row0, __nv_bfloat16* __restrict__ dst,
                                         float* __restrict__ unit) {
   __shared__ double tile[32][33];
+  __shared__ int ku_sh[32];
   const int x = blockIdx.z;
   const int p0 = blockIdx.x * 32, Q0 = blockIdx.y * 32;
   const int tx = threadIdx.x, ty = threadIdx.y;
@@ -354,21 +372,23 @@ __global__ void transpose_slice3_kernel(const double* __restrict__ W, int nQ, in
     const int Q = Q0 + j, p = p0 + tx;
     tile[j][tx] = (Q < nQ && p < N) ? w[(long long)Q * N + p] : 0.0;
   }
+  if (ty == 0) {
+    const int p = p0 + tx;
+    ku_sh[tx] = (p < N) ? tc::pow2_exp(unit_in[(long long)x * N + p]) : 0;
+  }
   __syncthreads();
   const long long plane = dst_rows * Qs;
   for (int j = ty; j < 32; j += 8) {
     const int p = p0 + j, Q = Q0 + tx;
     if (p >= N || Q >= Qs) continue;
-    const double* st = stats + 3 * ((long long)x * N + p);
-    const double u = tc::certified_unit(st[0], st[1], st[2], (double)Qs);
     const long long dr = row0 + (long long)x * N + p;
     __nv_bfloat16 h0, h1, h2;
-    tc::slice3(tile[tx][j] / u, h0, h1, h2);
+    tc::slice3_int(tile[tx][j], ku_sh[j], h0, h1, h2);
     __nv_bfloat16* d = dst + dr * Qs + Q;
     d[0] = h0;
     d[plane] = h1;
     d[2 * plane] = h2;
-    if (Q == 0) unit[dr] = (float)u;
+    if (Q == 0) unit[dr] = (float)unit_in[(long long)x * N + p];
   }
 }
 
@@ -422,7 +442,7 @@ int rot_limbs_slice4(const double* src, long long nrow, int ncol, long long ld, 
 int rot_transpose_slice3(const double* W, int nx, int nQ, int N, int Qs, double* stats,
                          long long dst_rows, long long row0, __nv_bfloat16* dst, float* unit,
                          cudaStream_t s) {
-  col_stats_kernel<<<dim3((N + 255) / 256, nx), 256, 0, s>>>(W, nQ, N, stats);
+  col_stats_kernel<<<dim3((N + 31) / 32, nx), 256, 0, s>>>(W, nQ, N, Qs, stats);
   transpose_slice3_kernel<<<dim3((N + 31) / 32, (Qs + 31) / 32, nx), dim3(32, 8), 0, s>>>(
       W, nQ, N, Qs, stats, dst_rows, row0, dst, unit);
   count_launch(2);

@@ -101,6 +101,24 @@ __device__ __forceinline__ void tma_load_4d(void* dst, const CUtensorMap* map, u
       : "memory");
 }
 
+// L2 prefetch of a tensor tile (no shared memory, no barrier): the producer
+// issues it some stages ahead of the load of the same tile, so that load
+// finds the tile in L2 rather than waiting on DRAM latency.
+__device__ __forceinline__ void tma_prefetch_3d(const CUtensorMap* map, int c0, int c1, int c2) {
+  asm volatile("cp.async.bulk.prefetch.tensor.3d.L2.global.tile [%0, {%1, %2, %3}];" ::"l"(
+                   reinterpret_cast<uint64_t>(map)),
+               "r"(c0), "r"(c1), "r"(c2)
+               : "memory");
+}
+
+__device__ __forceinline__ void tma_prefetch_4d(const CUtensorMap* map, int c0, int c1, int c2,
+                                                int c3) {
+  asm volatile("cp.async.bulk.prefetch.tensor.4d.L2.global.tile [%0, {%1, %2, %3, %4}];" ::"l"(
+                   reinterpret_cast<uint64_t>(map)),
+               "r"(c0), "r"(c1), "r"(c2), "r"(c3)
+               : "memory");
+}
+
 // ---- tensor memory ----
 __device__ __forceinline__ void tmem_alloc(uint32_t* dst, uint32_t ncols) {
   asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(
@@ -251,6 +269,101 @@ __device__ __forceinline__ void slice3(double u, __nv_bfloat16& h0, __nv_bfloat1
   h2 = __double2bfloat16(a2 * (1.0 / 65536.0));
 }
 
+// |x| as its IEEE bit pattern: non-negative doubles order like their bits as
+// unsigned integers, so a running max |x| runs on the integer pipe.
+__device__ __forceinline__ unsigned long long abs_bits(double x) {
+  return (unsigned long long)__double_as_longlong(x) & 0x7fffffffffffffffULL;
+}
+
+// ---- integer-pipe helpers (the FP64 pipe of this part issues about two
+// operations per clock per SM, so per-element FP64 work in a memory-bound
+// kernel or an epilogue costs more than the memory traffic itself) ----
+
+// Exponent returned for a unit that underflowed to zero in FP32 (rows whose
+// values lie below 2^-149 times their digits, e.g. far tails of decaying DF
+// factors): far below the double range, and small enough that a sum of two
+// such exponents cannot overflow an int.
+constexpr int kZeroUnitExp = -100000;
+
+// Exponent k of a power-of-two float u = 2^k (kZeroUnitExp for u = 0).
+__device__ __forceinline__ int pow2_exp(float u) {
+  const unsigned b = __float_as_uint(u);
+  const unsigned e = (b >> 23) & 0xffu;
+  if (e) return (int)e - 127;
+  return (b & 0x7fffffu) ? ilogbf(u) : kZeroUnitExp;
+}
+
+// Exponent k of a power-of-two double u = 2^k (u normal).
+__device__ __forceinline__ int pow2_exp(double u) {
+  return (int)(((unsigned long long)__double_as_longlong(u) >> 52) & 0x7ffULL) - 1023;
+}
+
+// f 2^k as a double, exactly: a float converts to a double by re-biasing the
+// exponent and widening the significand, done here on the integer pipe.
+// Zero (or k below the double range) gives 0; subnormal, non-finite or
+// out-of-range results take FP64 ldexp.
+__device__ __forceinline__ double scale_to_double(float f, int k) {
+  const unsigned b = __float_as_uint(f);
+  if ((b & 0x7fffffffu) == 0u || k < -1400) return 0.0;  // |f 2^k| < 2^-1270: zero
+  const int e = (int)((b >> 23) & 0xffu);
+  const int ed = e + 896 + k;  // 1023 - 127 = 896
+  if (e == 0 || e == 0xff || ed <= 0 || ed >= 0x7ff) return ldexp((double)f, k);
+  const unsigned hi = (b & 0x80000000u) | ((unsigned)ed << 20) | ((b & 0x7fffffu) >> 3);
+  return __hiloint2double((int)hi, (int)(b << 29));
+}
+
+// An FP32 upper bound of |x| (round toward +infinity of the significand, on the
+// integer pipe); |x| below the smallest normal float gives 2^-126, above the
+// float range +infinity.
+__device__ __forceinline__ float abs_up_float(double x) {
+  const unsigned long long b = abs_bits(x);
+  if (b == 0) return 0.0f;
+  const int ef = (int)(b >> 52) - 896;
+  if (ef >= 255) return __int_as_float(0x7f800000);
+  if (ef <= 0) return 1.17549435e-38f;  // 2^-126
+  unsigned fb = ((unsigned)ef << 23) | (unsigned)((b >> 29) & 0x7fffffULL);
+  if (b & 0x1fffffffULL) fb += 1u;  // a carry into the exponent is the right bound
+  return __uint_as_float(fb);
+}
+
+// Balanced base-256 fixed-point digits of v = x / 2^ku (the caller's unit
+// keeps |v| < 2^9): d0 the nearest integer to v, then each d_i the nearest
+// integer to 256 x the exact remainder, so v = d0 + d1/256 + ... + d_{ND-1}
+// 256^(1-ND) up to the last digit's rounding (<= 2^-(8 ND - 7)); ties round
+// away from zero.  Exact 64-bit integer arithmetic on the significand
+// (x = +-m 2^(e-1075)), no FP64 instruction; |d0| <= |v| + 1/2 as with rint,
+// and |d_i| <= 128 for i >= 1.
+template <int ND>
+__device__ __forceinline__ void fixed_digits(double x, int ku, int (&d)[ND]) {
+#pragma unroll
+  for (int i = 0; i < ND; ++i) d[i] = 0;
+  const unsigned long long b = (unsigned long long)__double_as_longlong(x);
+  const int e = (int)((b >> 52) & 0x7ffULL);
+  if (e == 0 || e == 0x7ff) return;  // zero, subnormal (< 2^-1022) or non-finite
+  long long m = (long long)((b & 0xfffffffffffffULL) | (1ULL << 52));
+  int t = 1075 + ku - e;  // v = m 2^-t, t >= 45 when |v| < 2^9
+  if (t > 62) {
+    if (t - 62 > 53) return;  // |v| < 2^-62: every digit rounds to zero
+    m >>= (t - 62);           // dropped bits could only decide exact ties
+    t = 62;
+  }
+  if (t < 8 * ND) t = 8 * ND;  // outside the caller's contract; keeps the shifts defined
+  long long q = (m + (1LL << (t - 1))) >> t;
+  long long r = m - q * (1LL << t);
+  d[0] = (int)q;
+#pragma unroll
+  for (int i = 1; i < ND; ++i) {
+    t -= 8;
+    q = (r + (1LL << (t - 1))) >> t;  // arithmetic shift: floor(r / 2^t + 1/2)
+    r -= q * (1LL << t);
+    d[i] = (int)q;
+  }
+  if (b >> 63) {
+#pragma unroll
+    for (int i = 0; i < ND; ++i) d[i] = -d[i];
+  }
+}
+
 __device__ __forceinline__ void slice3f(float u, __nv_bfloat16& h0, __nv_bfloat16& h1,
                                         __nv_bfloat16& h2) {
   const float a0 = rintf(u);
@@ -291,6 +404,49 @@ __host__ __device__ __forceinline__ double certified_unit(double m, double s2, d
   double u = slice_unit(m, 8);
   while (s2 / (u * u) + s1 / u + 0.25 * n > 16777216.0) u *= 2.0;
   return u;
+}
+
+// Row statistics for certified_unit on the integer and FP32 pipes: max |x|
+// (bits), and upper bounds of sum x^2 and sum |x| (FP32, every operation
+// rounded toward +infinity, so the bounds hold however the sums are split).
+struct RowStats {
+  unsigned long long mb = 0;
+  float s2 = 0.0f, s1 = 0.0f;
+  __device__ __forceinline__ void add(double x) {
+    mb = max(mb, abs_bits(x));
+    const float a = abs_up_float(x);
+    s2 = __fadd_ru(s2, __fmul_ru(a, a));
+    s1 = __fadd_ru(s1, a);
+  }
+  __device__ __forceinline__ void merge(unsigned long long mb2, float s22, float s12) {
+    mb = max(mb, mb2);
+    s2 = __fadd_ru(s2, s22);
+    s1 = __fadd_ru(s1, s12);
+  }
+  __device__ __forceinline__ void warp_reduce() {
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1)
+      merge((unsigned long long)__shfl_xor_sync(0xffffffffu, (long long)mb, o),
+            __shfl_xor_sync(0xffffffffu, s2, o), __shfl_xor_sync(0xffffffffu, s1, o));
+  }
+  // certified_unit from the bounds; false if a bound overflowed the float
+  // range (|x| >= 2^64 somewhere), where the caller recomputes in FP64
+  __device__ __forceinline__ bool unit(double n, double& u) const {
+    if (!(s2 <= 3.4e38f) || !(s1 <= 3.4e38f)) return false;
+    u = certified_unit(__longlong_as_double((long long)mb), (double)s2, (double)s1, n);
+    return true;
+  }
+};
+
+// Three limbs of x / 2^ku (slice3's layout: h0 integer, h1 in 2^-8 Z, h2 in
+// 2^-16 Z) from fixed_digits<3>.
+__device__ __forceinline__ void slice3_int(double x, int ku, __nv_bfloat16& h0,
+                                           __nv_bfloat16& h1, __nv_bfloat16& h2) {
+  int d[3];
+  fixed_digits<3>(x, ku, d);
+  h0 = __float2bfloat16_rn((float)d[0]);
+  h1 = __float2bfloat16_rn((float)d[1] * (1.0f / 256.0f));
+  h2 = __float2bfloat16_rn((float)d[2] * (1.0f / 65536.0f));
 }
 
 }  // namespace tc

@@ -1,0 +1,104 @@
+"""The nmo = 1000, naux = 4000 workload (synthetic system seed 3, the scale of
+the paper's large-system runs): the moment build at full size.
+
+At the steady-state pole shape (3000 poles, 1200 occupied) one element of U
+sums over o^2 v = 2.6e9 pole triples, so neither the oracle nor the FP64 path
+can check the full build in a test's time.  Instead:
+
+* pole slice: a seeded 5% of the occupied and of the virtual poles of that
+  pole set (60 + 90 poles; N = 1000 and n_Q = 4000 unchanged) through both
+  precisions against the oracle's ``build_moments`` on the same slice, element
+  by element (FP64 1e-10, split-BF16 1e-7 of max |U|).  A pole slice is a
+  partial sum of the full moments over the chosen poles (slice additivity);
+* the full steady-state build in split BF16 with properties that hold at any
+  size: U_<^(0), U_>^(0) positive semidefinite (sums of (1/2) S S^T +
+  (3/2) D D^T), U_<^(1) negative and U_>^(1) positive semidefinite (every
+  weight e_i + e_j - e_a < 0 < e_a + e_b - e_i for these pole energies), and
+  finite; the build time is printed.
+
+About 64 GB of host memory for the inputs and 170 GB on the device; run with
+AGF2_LARGE=1 (skipped otherwise).
+"""
+import json
+import os
+import time
+
+import numpy as np
+import pytest
+
+from oracle import agf2_oracle as O
+from paper_2106_03508_gb300.synth import make_config, random_poles
+
+pytestmark = [pytest.mark.gpu,
+              pytest.mark.skipif(os.environ.get("AGF2_LARGE") != "1",
+                                 reason="nmo=1000 workload: set AGF2_LARGE=1")]
+
+NQ, NOCC_POLES, POLE_SEED = 3000, 1200, 17
+
+
+@pytest.fixture(scope="module")
+def c5():
+    import torch
+    t = time.time()
+    s = make_config("c5")
+    Ld = torch.from_numpy(s.L).cuda()
+    print(f"\nc5 inputs generated and on the device in {time.time() - t:.1f} s", flush=True)
+    e, C, mu = random_poles(s.nmo, NQ, NOCC_POLES, POLE_SEED)
+    yield s, Ld, e, C, mu
+    del Ld
+    torch.cuda.empty_cache()
+
+
+def _build(lib, h, s, Ld, e, C, mu, prec):
+    import torch
+    N, nq = s.nmo, len(e)
+    ed = torch.from_numpy(np.ascontiguousarray(e)).cuda()
+    Cd = torch.from_numpy(np.ascontiguousarray(C)).cuda()
+    Uh = torch.empty(2, N, N, dtype=torch.float64, device="cuda")
+    Up = torch.empty_like(Uh)
+    torch.cuda.synchronize()
+    t = time.perf_counter()
+    lib.agf2_build_moments(h.h, Ld.data_ptr(), s.naux, N, ed.data_ptr(), Cd.data_ptr(), nq, mu,
+                           1, prec, Uh.data_ptr(), Up.data_ptr())
+    torch.cuda.synchronize()
+    return Uh.cpu().numpy(), Up.cpu().numpy(), time.perf_counter() - t
+
+
+def test_c5_pole_slice_vs_oracle(cuda_handle, agf2_lib, c5):
+    s, Ld, e, C, mu = c5
+    rng = np.random.default_rng(5)
+    occ = np.flatnonzero(e < mu)
+    vir = np.flatnonzero(~(e < mu))
+    pick = np.sort(np.concatenate([rng.choice(occ, len(occ) // 20, replace=False),
+                                   rng.choice(vir, len(vir) // 20, replace=False)]))
+    es, Cs = e[pick], np.ascontiguousarray(C[:, pick])
+    t = time.time()
+    ref_h, ref_p = O.build_moments(s.L, es, Cs, mu, 1)
+    t_or = time.time() - t
+    for prec, rtol in ((agf2_lib.AGF2_FP64, 1e-10), (agf2_lib.AGF2_BF16X3, 1e-7)):
+        Uh, Up, dt = _build(agf2_lib, cuda_handle, s, Ld, es, Cs, mu, prec)
+        worst = 0.0
+        for U, ref in ((Uh, ref_h), (Up, ref_p)):
+            for n in range(2):
+                worst = max(worst, np.max(np.abs(U[n] - ref[n])) / np.max(np.abs(ref[n])))
+        print(json.dumps({"case": "c5 pole slice", "poles": len(pick), "precision": int(prec),
+                          "gpu_s": dt, "oracle_s": t_or, "max_rel_err": worst}), flush=True)
+        assert worst < rtol
+
+
+def test_c5_steady_state_full_build(cuda_handle, agf2_lib, c5):
+    s, Ld, e, C, mu = c5
+    Uh, Up, dt = _build(agf2_lib, cuda_handle, s, Ld, e, C, mu, agf2_lib.AGF2_BF16X3)
+    o = int(np.sum(e < mu))
+    v = len(e) - o
+    N, naux = s.nmo, s.naux
+    F = N * o * v * (o + v) * (2.0 * naux + 4.0 * N)
+    assert np.all(np.isfinite(Uh)) and np.all(np.isfinite(Up))
+    ev = {}
+    for name, U, sign in (("hole_U0", Uh[0], 1), ("part_U0", Up[0], 1),
+                          ("hole_U1", Uh[1], -1), ("part_U1", Up[1], 1)):
+        w = np.linalg.eigvalsh(sign * U)
+        ev[name] = (float(w[0]), float(w[-1]))
+        assert w[0] > -1e-6 * w[-1], (name, w[0], w[-1])
+    print(json.dumps({"case": "c5 steady state", "o": o, "v": v, "seconds": dt,
+                      "tflops_algorithmic": F / dt / 1e12, "eig_min_max": ev}), flush=True)
