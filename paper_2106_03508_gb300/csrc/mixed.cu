@@ -167,30 +167,6 @@ __device__ __forceinline__ void load_a(const CUtensorMap* mapA, uint8_t* dst, ui
     tc::tma_load_3d(dst, mapA, bar, ks * BK, s.a_row, s.a_plane * 3 + limb);
 }
 
-// L2 prefetch of everything one K stage of a segment loads (the producer runs
-// it PF_STAGES ahead of the loads).
-template <int MODE>
-__device__ __forceinline__ void prefetch_stage(const CUtensorMap* mapA, const CUtensorMap* mapB,
-                                               const Params& P, const Segment& s, int ks) {
-#pragma unroll
-  for (int l = 0; l < 3; ++l) {
-    if (MODE == MODE_PAIR) {
-      tc::tma_prefetch_3d(mapA, ks * BK, s.a_row, l * P.n_out + s.a_idx);
-      if (P.hole)
-        tc::tma_prefetch_4d(mapB, ks * BK, s.b_row, s.b_idx, l);
-      else
-        tc::tma_prefetch_4d(mapB, ks * BK, s.b_idx, s.b_row, l);
-    } else {
-      tc::tma_prefetch_3d(mapA, ks * BK, s.a_row, s.a_plane * 3 + l);
-      tc::tma_prefetch_3d(mapB, ks * BK, s.b_row, l);
-    }
-  }
-}
-
-// Stages between an L2 prefetch and the load of the same data (6 x 48 KB per
-// SM in flight, about a third of L2 over all SMs).
-constexpr int PF_STAGES = 6;
-
 // Work of one tile: one K segment into one accumulator set (nseg = 0: no
 // work, the tile is skipped by every role).
 struct TileWork {
@@ -315,31 +291,6 @@ gemm6_kernel(const __grid_constant__ CUtensorMap mapA, const __grid_constant__ C
     // ---------------- TMA producer ----------------
     tc::tma_prefetch(&mapA);
     tc::tma_prefetch(&mapB);
-    // L2 prefetch cursor, PF_STAGES stages ahead of the loads (across tiles)
-    int pf_tile = first_tile<MODE>(), pf_ks = 0;
-    TileWork pw;
-    bool pf_live = false;
-    auto pf_seek = [&]() {  // first stage of the next tile with work, from pf_tile on
-      pf_live = false;
-      for (; pf_tile < P.ntiles; pf_tile = next_tile<MODE>(pf_tile)) {
-        pw = decode_tile<MODE>(P, pf_tile);
-        if (pw.nseg > 0 && pw.seg[0].kbeg < pw.seg[0].kend) {
-          pf_ks = pw.seg[0].kbeg;
-          pf_live = true;
-          return;
-        }
-      }
-    };
-    auto pf_step = [&]() {
-      if (!pf_live) return;
-      prefetch_stage<MODE>(&mapA, &mapB, P, pw.seg[0], pf_ks);
-      if (++pf_ks >= pw.seg[0].kend) {
-        pf_tile = next_tile<MODE>(pf_tile);
-        pf_seek();
-      }
-    };
-    pf_seek();
-    for (int i = 0; i < PF_STAGES; ++i) pf_step();
     int t = 0;
     bool ok = true;
     for (int tile = first_tile<MODE>(); tile < P.ntiles && ok; tile = next_tile<MODE>(tile)) {
@@ -368,7 +319,6 @@ gemm6_kernel(const __grid_constant__ CUtensorMap mapA, const __grid_constant__ C
             }
           }
           issued_sh = t + 1;
-          pf_step();
         }
       }
     }
