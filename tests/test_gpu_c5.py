@@ -16,7 +16,7 @@ can check the full build in a test's time.  Instead:
   weight e_i + e_j - e_a < 0 < e_a + e_b - e_i for these pole energies), and
   finite; the build time is printed.
 
-About 64 GB of host memory for the inputs and 170 GB on the device; run with
+About 64 GB of host memory for the inputs and ~200 GB on the device; run with
 AGF2_LARGE=1 (skipped otherwise).
 """
 import json
@@ -87,8 +87,10 @@ def test_c5_pole_slice_vs_oracle(cuda_handle, agf2_lib, c5):
 
 
 def test_c5_steady_state_full_build(cuda_handle, agf2_lib, c5):
+    import torch
     s, Ld, e, C, mu = c5
     Uh, Up, dt = _build(agf2_lib, cuda_handle, s, Ld, e, C, mu, agf2_lib.AGF2_BF16X3)
+    free, total = torch.cuda.mem_get_info()
     o = int(np.sum(e < mu))
     v = len(e) - o
     N, naux = s.nmo, s.naux
@@ -101,4 +103,5 @@ def test_c5_steady_state_full_build(cuda_handle, agf2_lib, c5):
         ev[name] = (float(w[0]), float(w[-1]))
         assert w[0] > -1e-6 * w[-1], (name, w[0], w[-1])
     print(json.dumps({"case": "c5 steady state", "o": o, "v": v, "seconds": dt,
-                      "tflops_algorithmic": F / dt / 1e12, "eig_min_max": ev}), flush=True)
+                      "tflops_algorithmic": F / dt / 1e12, "device_in_use_gb": (total - free) / 1e9,
+                      "eig_min_max": ev}), flush=True)
