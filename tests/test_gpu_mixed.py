@@ -57,3 +57,32 @@ def test_moments_mixed_exact_integer_sums_flat_rows(cuda_handle, agf2_lib):
     for n in range(2):
         assert rel(Uh[n], Rh[n]) < MIXED_RTOL, (n, rel(Uh[n], Rh[n]))
         assert rel(Up[n], Rp[n]) < MIXED_RTOL, (n, rel(Up[n], Rp[n]))
+
+
+def test_moments_mixed_underflowing_row_units(cuda_handle, agf2_lib):
+    """naux = 4000 with the generator's exp(-Q/24) decay: rows of the DF
+    factors past Q ~ 2300 lie below 2^-142, so their FP32 slicing units
+    underflow to zero in the rotation; those rows must contribute nothing
+    (their true contribution is below 2^-140 relative) rather than enter the
+    exponent arithmetic of the rotation's epilogue."""
+    s = make_system(40, 8, 4000, 12)
+    e, C, mu = random_poles(40, 120, 48, 19)
+    Rh, Rp = O.build_moments(s.L, e, C, mu)
+    for scale in (1.0, 1.0 / 16.0):
+        Uh, Up = gpu_moments(agf2_lib, cuda_handle, s.L, e, C * scale, mu,
+                             precision=agf2_lib.AGF2_BF16X3)
+        for n in range(2):
+            assert rel(Uh[n] / scale ** 4, Rh[n]) < 1e-7, (scale, n, rel(Uh[n] / scale ** 4, Rh[n]))
+            assert rel(Up[n] / scale ** 4, Rp[n]) < 1e-7, (scale, n, rel(Up[n] / scale ** 4, Rp[n]))
+
+
+def test_moments_mixed_power_of_two_scaling(cuda_handle, agf2_lib):
+    """Every unit of the split path is a power of two, so scaling the pole
+    couplings by 2^-4 scales U by exactly 2^-16 (the limbs are unchanged):
+    the two builds agree to the FP64 atomics' summation-order rounding."""
+    s = make_system(70, 14, 300, 21)
+    e, C, mu = random_poles(70, 210, 83, 23)
+    U1 = gpu_moments(agf2_lib, cuda_handle, s.L, e, C, mu, precision=agf2_lib.AGF2_BF16X3)
+    U2 = gpu_moments(agf2_lib, cuda_handle, s.L, e, C / 16.0, mu, precision=agf2_lib.AGF2_BF16X3)
+    for a, b in zip(U1, U2):
+        assert np.max(np.abs(b * 65536.0 - a)) <= 1e-12 * np.max(np.abs(a))
