@@ -72,17 +72,19 @@ def test_moments_mixed_underflowing_row_units(cuda_handle, agf2_lib):
         Uh, Up = gpu_moments(agf2_lib, cuda_handle, s.L, e, C * scale, mu,
                              precision=agf2_lib.AGF2_BF16X3)
         for n in range(2):
-            assert rel(Uh[n] / scale ** 4, Rh[n]) < 1e-7, (scale, n, rel(Uh[n] / scale ** 4, Rh[n]))
-            assert rel(Up[n] / scale ** 4, Rp[n]) < 1e-7, (scale, n, rel(Up[n] / scale ** 4, Rp[n]))
+            # (pi|ja) carries three pole couplings, so U scales as the sixth power
+            assert rel(Uh[n] / scale ** 6, Rh[n]) < 1e-7, (scale, n, rel(Uh[n] / scale ** 6, Rh[n]))
+            assert rel(Up[n] / scale ** 6, Rp[n]) < 1e-7, (scale, n, rel(Up[n] / scale ** 6, Rp[n]))
 
 
 def test_moments_mixed_power_of_two_scaling(cuda_handle, agf2_lib):
     """Every unit of the split path is a power of two, so scaling the pole
-    couplings by 2^-4 scales U by exactly 2^-16 (the limbs are unchanged):
-    the two builds agree to the FP64 atomics' summation-order rounding."""
+    couplings by 2^-4 scales U (sixth order in the couplings: three per
+    (pi|ja)) by exactly 2^-24 with unchanged limbs: the two builds agree to
+    the FP64 atomics' summation-order rounding."""
     s = make_system(70, 14, 300, 21)
     e, C, mu = random_poles(70, 210, 83, 23)
     U1 = gpu_moments(agf2_lib, cuda_handle, s.L, e, C, mu, precision=agf2_lib.AGF2_BF16X3)
     U2 = gpu_moments(agf2_lib, cuda_handle, s.L, e, C / 16.0, mu, precision=agf2_lib.AGF2_BF16X3)
     for a, b in zip(U1, U2):
-        assert np.max(np.abs(b * 65536.0 - a)) <= 1e-12 * np.max(np.abs(a))
+        assert np.max(np.abs(b * 2.0 ** 24 - a)) <= 1e-12 * np.max(np.abs(a))
