@@ -70,7 +70,7 @@ def workload_desc(cfg, nmom=1):
 # ---------------------------------------------------------------------------
 # CPU oracle sample (cpu_baseline and --impl reference)
 # ---------------------------------------------------------------------------
-FOCK_CAP = 100                 # agf2_fock_opts default max_cycle (reached by the c2/c3 loops)
+FOCK_CAP = 50                  # agf2_fock_opts default max_cycle (reached by the c2/c3 loops)
 ORACLE_FRACTION = 1.0 / 60.0   # share of the outer summed indices timed per sample
 
 

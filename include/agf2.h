@@ -138,7 +138,7 @@ int agf2_eigh_physical(agf2_handle h, const double* A, int n, int nphys, double*
 
 typedef struct {
     double tol_D;      /* convergence: max |D_new - D| (default 1e-10)        */
-    int    max_cycle;  /* Fock cycles (default 100)                           */
+    int    max_cycle;  /* Fock cycles (default 50)                            */
     double shift_tol;  /* |n(delta) - nelec| target of the shift (1e-11)      */
     double damping;    /* linear mixing of F before DIIS starts (0.3)         */
     int    diis_start; /* first cycle whose pair enters DIIS (10)             */

@@ -454,7 +454,7 @@ def diis_extrapolate(hist):
     return sum(c[a] * (hist[a][0] + hist[a][1]) for a in range(m))
 
 
-def fock_loop(h, L, nelec, E_se, v_se, D, tol_D=1e-10, max_cycle=100, shift_tol=1e-11,
+def fock_loop(h, L, nelec, E_se, v_se, D, tol_D=1e-10, max_cycle=50, shift_tol=1e-11,
               damping=0.3, diis_start=10, diis_space=6):
     """Relax D = 2 C_occ C_occ^T self-consistently with F[D], keeping the
     electron count through a common shift of the auxiliary energies.
@@ -551,7 +551,7 @@ class RunResult:
 
 
 def run(h, L, nelec, eps0, max_iter=50, conv_tol=1e-8, nmom=1, fock_tol=1e-10,
-        fock_max_cycle=100, diis_space=0, diis_start=2, mix=1.0, keep_moments=False, D0=None):
+        fock_max_cycle=50, diis_space=0, diis_start=2, mix=1.0, keep_moments=False, D0=None):
     """AGF2 from the HF reference (Eq. gf_hf).  With D0 (the reference
     density in the basis of h and L) the initial poles and couplings are the
     eigenpairs of F[D0]; without it the basis is that of the reference's

@@ -916,7 +916,7 @@ FockOut fock_loop_impl(agf2_context* ctx, const double* h, const double* L, int 
 agf2_fock_opts fock_defaults() {
   agf2_fock_opts o;
   o.tol_D = 1e-10;
-  o.max_cycle = 100;
+  o.max_cycle = 50;
   o.shift_tol = 1e-11;
   o.damping = 0.3;
   o.diis_start = 10;

@@ -18,12 +18,13 @@ def test_batched_uneven_systems_match_oracle(cuda_handle, agf2_lib):
         s = make_system(nmo, nocc, naux, seed)
         s.L *= 0.5
         h = O.hcore_from_mo_energies(s.eps, s.L, s.nocc)
-        refs.append(O.run(h, s.L, s.nelec, s.eps, max_iter=30))
+        refs.append(O.run(h, s.L, s.nelec, s.eps, max_iter=30, fock_max_cycle=300))
         L, hc, eps = (torch.from_numpy(np.ascontiguousarray(x)).cuda() for x in (s.L, h, s.eps))
         keep += [L, hc, eps]
         systems.append((hc.data_ptr(), L.data_ptr(), None, naux, nmo, s.nelec))
     o = agf2_lib.agf2_opts_default()
     o.max_iter = 30
+    o.fock.max_cycle = 300
     rc, outs, st = agf2_lib.agf2_run_batched(cuda_handle.h, systems, o, nworkers=3)
     for out, ref, status in zip(outs, refs, st):
         assert status in (agf2_lib.AGF2_OK, agf2_lib.AGF2_ERR_NO_CONVERGENCE)
