@@ -1,9 +1,8 @@
 // tcgen05 / TMA / mbarrier building blocks for sm_103a (inline PTX).
 //
 // Conventions of the split-BF16 GEMM mainloop used by the moment build:
-//  - operands are K-major BF16 tiles loaded by TMA with 128-byte (64 K
-//    elements per row, 1024 B atoms) or 64-byte (32 per row, 512 B atoms)
-//    swizzling;
+//  - operands are K-major BF16 tiles loaded by TMA with 64-byte swizzling
+//    (32 K elements per row, 8-row atoms of 512 B);
 //  - one elected thread issues tcgen05.mma (kind::f16, BF16 inputs, FP32
 //    accumulator in tensor memory), M = 128 rows, N = BN columns, K = 16 per
 //    instruction;
@@ -132,20 +131,8 @@ __host__ __device__ constexpr uint32_t idesc_bf16_f32(int M, int N) {
          | ((uint32_t)(M >> 4) << 24);          // M / 16
 }
 
-// Shared-memory matrix descriptor: K-major tile, 128-byte swizzle, rows of
-// 128 B, 8-row atoms 1024 B apart (stride byte offset), sm_100 version bits.
-__device__ __forceinline__ uint64_t sdesc_sw128(uint32_t saddr) {
-  uint64_t d = 0;
-  d |= (uint64_t)((saddr & 0x3FFFFu) >> 4);
-  d |= (uint64_t)1 << 16;             // leading byte offset (unused for this layout)
-  d |= (uint64_t)(1024u >> 4) << 32;  // stride byte offset
-  d |= (uint64_t)1 << 46;             // descriptor version
-  d |= (uint64_t)2 << 61;             // SWIZZLE_128B
-  return d;
-}
-
-// Same for 64-byte swizzled K-major tiles (rows of 64 B = 32 BF16, 8-row atoms
-// of 512 B).
+// Shared-memory matrix descriptor: K-major tile, 64-byte swizzle, rows of 64 B
+// (32 BF16), 8-row atoms 512 B apart (stride byte offset), sm_100 version bits.
 __device__ __forceinline__ uint64_t sdesc_sw64(uint32_t saddr) {
   uint64_t d = 0;
   d |= (uint64_t)((saddr & 0x3FFFFu) >> 4);
@@ -173,35 +160,6 @@ __device__ __forceinline__ void umma_commit(uint64_t* bar) {
       : "memory");
 }
 
-// 32 consecutive FP32 columns of this thread's TMEM lane.
-__device__ __forceinline__ void tmem_ld32(uint32_t taddr, float* v) {
-  uint32_t r[32];
-  asm volatile(
-      "tcgen05.ld.sync.aligned.32x32b.x32.b32 "
-      "{%0, %1, %2, %3, %4, %5, %6, %7, %8, %9, %10, %11, %12, %13, %14, %15, "
-      "%16, %17, %18, %19, %20, %21, %22, %23, %24, %25, %26, %27, %28, %29, %30, %31}, [%32];"
-      : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]),
-        "=r"(r[7]), "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]),
-        "=r"(r[14]), "=r"(r[15]), "=r"(r[16]), "=r"(r[17]), "=r"(r[18]), "=r"(r[19]),
-        "=r"(r[20]), "=r"(r[21]), "=r"(r[22]), "=r"(r[23]), "=r"(r[24]), "=r"(r[25]),
-        "=r"(r[26]), "=r"(r[27]), "=r"(r[28]), "=r"(r[29]), "=r"(r[30]), "=r"(r[31])
-      : "r"(taddr));
-  asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
-#pragma unroll
-  for (int i = 0; i < 32; ++i) v[i] = __uint_as_float(r[i]);
-}
-
-// 4 consecutive FP32 columns of this thread's TMEM lane.
-__device__ __forceinline__ void tmem_ld4(uint32_t taddr, float* v) {
-  uint32_t r[4];
-  asm volatile("tcgen05.ld.sync.aligned.32x32b.x4.b32 {%0, %1, %2, %3}, [%4];"
-               : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3])
-               : "r"(taddr));
-  asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
-#pragma unroll
-  for (int i = 0; i < 4; ++i) v[i] = __uint_as_float(r[i]);
-}
-
 // 8 consecutive FP32 columns of this thread's TMEM lane.
 __device__ __forceinline__ void tmem_ld8(uint32_t taddr, float* v) {
   uint32_t r[8];
@@ -215,7 +173,8 @@ __device__ __forceinline__ void tmem_ld8(uint32_t taddr, float* v) {
   for (int i = 0; i < 8; ++i) v[i] = __uint_as_float(r[i]);
 }
 
-// 16 consecutive FP32 columns of this thread's TMEM lane.
+// 16 consecutive FP32 columns of this thread's TMEM lane (32x32b shape: warp
+// w of a warpgroup reads lanes 32 (w % 4) .. 32 (w % 4) + 31).
 __device__ __forceinline__ void tmem_ld16(uint32_t taddr, float* v) {
   uint32_t r[16];
   asm volatile(
@@ -237,19 +196,10 @@ __device__ __forceinline__ void tmem_ld16(uint32_t taddr, float* v) {
 //   h2 in 2^-16 Z (|h1|, |h2| <= 128 units of their grid),
 // all exactly representable in BF16.  Products h0*h0' are integers of
 // magnitude <= R^2, so a sum of K of them is exact in the FP32 tensor-core
-// accumulator whenever R^2 K <= 2^24; the caller picks rbits from the
-// accumulation length (hi_bits).  The remaining limb products are kept in a
-// separate accumulator.
-__device__ __forceinline__ void slice3(double u, __nv_bfloat16& h0, __nv_bfloat16& h1,
-                                       __nv_bfloat16& h2) {
-  const double a0 = rint(u);
-  const double r1 = (u - a0) * 256.0;
-  const double a1 = rint(r1);
-  const double a2 = rint((r1 - a1) * 256.0);
-  h0 = __double2bfloat16(a0);
-  h1 = __double2bfloat16(a1 * (1.0 / 256.0));
-  h2 = __double2bfloat16(a2 * (1.0 / 65536.0));
-}
+// accumulator whenever R^2 K <= 2^24 (or, for any K, under a row
+// certificate: certified_unit).  The remaining limb products are kept in a
+// separate accumulator.  slice3f cuts FP32 values; slice3_int cuts FP64
+// values on the integer pipe (fixed_digits).
 
 // |x| as its IEEE bit pattern: non-negative doubles order like their bits as
 // unsigned integers, so a running max |x| runs on the integer pipe.
