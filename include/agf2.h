@@ -11,7 +11,10 @@
  *    synchronous with respect to the host: outputs are complete on return.
  *  - The library owns only the workspace held by the handle (grown on
  *    demand, freed by agf2_destroy).  Work is issued on the handle's stream
- *    (agf2_set_stream; default: the legacy default stream).
+ *    (agf2_set_stream; default: the legacy default stream); the AGF2_BF16X3
+ *    moment build also forks part of its work onto a second stream owned by
+ *    the handle and joins it back into the handle's stream with events
+ *    before it returns.
  *  - Every function returns an int status (AGF2_OK = 0).  On failure the
  *    outputs are unspecified and agf2_last_error(handle) returns a message.
  *    No C++ exception crosses the ABI.
@@ -82,6 +85,10 @@ int agf2_hcore_from_mo_energies(agf2_handle h, const double* L, int naux, int nm
  *   U_hole [nmom+1][nmo][nmo] out  (symmetrised)
  *   U_part [nmom+1][nmo][nmo] out  (symmetrised)
  * Needs at least one occupied and one virtual pole (else INVALID_ARG).
+ * AGF2_BF16X3 holds the rotated integrals as three-limb BF16 planes,
+ * 6 (nqmo nmo + o v) ceil32(naux) bytes (o, v the occupied / virtual pole
+ * counts), plus the DF factors' four-limb planes and ~2 GB of pair-block
+ * buffers; at nmo = 1000, naux = 4000, 3000 poles about 160 GB of workspace.
  */
 int agf2_build_moments(agf2_handle h, const double* L, int naux, int nmo,
                        const double* e, const double* C, int nqmo, double mu,
