@@ -784,6 +784,7 @@ void mixed_workspace_destroy(void* w) {
     const cudaError_t e_ = (call);                                             \
     if (e_ != cudaSuccess) {                                                   \
       err = std::string(#call ": ") + cudaGetErrorString(e_);                  \
+      if (W.side) cudaStreamSynchronize(W.side); /* no side work outlives us */ \
       return AGF2_ERR_CUDA;                                                    \
     }                                                                          \
   } while (0)
@@ -1113,7 +1114,10 @@ int mixed_build_moments(const double* L, int naux, int N, const double* Co, cons
       CK_SIDE(cudaEventRecord(W.ev_comb[cur], W.side));
       if (pend.valid) {
         const int rc = launch_moment(pend);
-        if (rc != AGF2_OK) return rc;
+        if (rc != AGF2_OK) {
+          cudaStreamSynchronize(W.side);  // the slicing passes still queued there
+          return rc;
+        }
       }
       pend.valid = true;
       pend.buf = cur;
@@ -1122,7 +1126,10 @@ int mixed_build_moments(const double* L, int naux, int N, const double* Co, cons
     }
     if (pend.valid) {
       const int rc = launch_moment(pend);
-      if (rc != AGF2_OK) return rc;
+      if (rc != AGF2_OK) {
+        cudaStreamSynchronize(W.side);
+        return rc;
+      }
     }
   }
   {
