@@ -41,6 +41,8 @@ Readings taken where the paper is silent (identical on the CUDA side):
   - mu: aufbau count k minimising |2 sum_{x<k} |C_x|^2 - nelec| and mu at the
     HOQMO/LUQMO midpoint; auxiliary energies shifted by a common delta found
     by bisection on n(delta; k fixed) - nelec;
+  - the Fock loop stops when max|dD| < tol_D or after max_cycle cycles
+    (50 by default);
   - two-body energy: Galitskii-Migdal pole form with the occupied QMOs and the
     particle-sector auxiliaries;
   - IP = -e_HOQMO, EA = -e_LUQMO.
